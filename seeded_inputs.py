@@ -1,0 +1,97 @@
+"""Seeded synthetic inputs shared by the oracle side and the GPU side.
+
+This module holds workload definitions and random number generation only --
+none of the method's arithmetic.  Both the tests (oracle and GPU paths) and
+the benchmark draw their inputs from here, so that the two sides always see
+identical data.
+
+Workloads (matrix, batch, distributions) follow the configurations this
+project measures; workload ``i`` (1-based) uses numpy PCG64 seed ``i - 1``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Dilation/pattern matrices of the measured workloads.
+M_SMALL_2D = [[64, 16], [-16, 64]]                          # det 4352, cycles (16, 272)
+M_BATCHED_2D = [[4096, 1024], [0, 4096]]                    # det 2^24, cycles (1024, 16384)
+M_AUTOGRAD_3D = [[256, 64, 0], [0, 256, 32], [0, 0, 256]]   # det 2^24, cycles (32, 64, 8192)
+M_AUTOGRAD_TINY = [[4, 1, 0], [0, 4, 1], [0, 0, 4]]         # det 64, one cycle of 64
+M_WAVELET_2D = [[1024, 1024], [-1024, 1024]]                # 2^10 [[1,1],[-1,1]], det 2^21
+J_DIAG_A = [[1, 1], [-1, 1]]
+J_DIAG_B = [[1, -1], [1, 1]]
+
+WORKLOADS = {
+    "small_2d": dict(M=M_SMALL_2D, batch=1, seed=0),
+    "batched_2d": dict(M=M_BATCHED_2D, batch=8, seed=1),
+    "autograd_3d": dict(M=M_AUTOGRAD_3D, batch=4, seed=2),
+    "wavelet_2d": dict(M=M_WAVELET_2D, batch=16, seed=3, levels=12),
+    "uneven_mix": dict(n_patterns=4096, seed=4),
+}
+
+SAMPLE_SEED = 12345
+
+
+def wavelet_dilations(levels: int):
+    """Dilations J_1, J_2, ... alternating [[1,1],[-1,1]] and [[1,-1],[1,1]]."""
+    return [J_DIAG_A if l % 2 == 0 else J_DIAG_B for l in range(levels)]
+
+
+def complex_normal(batch: int, n: int, seed: int, dtype=np.complex64) -> np.ndarray:
+    """[batch, n] complex values whose real and imaginary parts are i.i.d. N(0,1)."""
+    rng = np.random.default_rng(seed)
+    re = rng.standard_normal((batch, n))
+    im = rng.standard_normal((batch, n))
+    return (re + 1j * im).astype(dtype)
+
+
+def uniform01(shape, seed: int, dtype=np.float64) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.random(shape).astype(dtype)
+
+
+def sample_slots(m: int, n: int = 4096, seed: int = SAMPLE_SEED) -> np.ndarray:
+    """n distinct slot indices in [0, m), sorted (all of them when n >= m)."""
+    if n >= m:
+        return np.arange(m, dtype=np.int64)
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(m, size=n, replace=False).astype(np.int64))
+
+
+def random_upper_triangular(rng, d: int, lo: int, hi: int):
+    """Upper-triangular integer matrix, diagonal uniform in [lo, hi],
+    entry (r, c), r < c, uniform in [0, M_rr)."""
+    M = [[0] * d for _ in range(d)]
+    for r in range(d):
+        M[r][r] = int(rng.integers(lo, hi + 1))
+    for r in range(d):
+        for c in range(r + 1, d):
+            M[r][c] = int(rng.integers(0, M[r][r]))
+    return M
+
+
+def uneven_mix(n_patterns: int = 4096, seed: int = 4, max_det: int = 1 << 20,
+               lo: int = 16, hi: int = 512):
+    """Patterns of the uneven serving-style mix: d uniform in {2, 3}, upper
+    triangular, diagonals uniform in [lo, hi], off-diagonals in [0, diag),
+    resampled until the determinant (product of the diagonal) is <= max_det."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n_patterns:
+        d = int(rng.integers(2, 4))
+        M = random_upper_triangular(rng, d, lo, hi)
+        prod = 1
+        for r in range(d):
+            prod *= M[r][r]
+        if prod <= max_det:
+            out.append(M)
+    return out
+
+
+def random_regular_matrix(rng, d: int, amax: int, max_det: int):
+    """A random integer matrix with 0 < |det| <= max_det (rejection sampling)."""
+    while True:
+        M = [[int(rng.integers(-amax, amax + 1)) for _ in range(d)] for _ in range(d)]
+        D = int(round(np.linalg.det(np.array(M, dtype=np.float64))))
+        if 0 < abs(D) <= max_det:
+            return M

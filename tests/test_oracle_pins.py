@@ -1,0 +1,373 @@
+"""Pins for the CPU oracle: every check compares it with something other than
+itself -- the textbook DFT (numpy, a library call), brute force with exact
+rational phases, closed-form identities of the paper, or printed values
+(Table 1, Example 1).  CPU only."""
+import cmath
+import itertools
+import math
+import os
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import lattice as L
+import seeded_inputs as SI
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_c(m, batch=1, seed=0):
+    return SI.complex_normal(batch, m, seed, dtype=np.complex128)
+
+
+def _gauss_jordan_inverse(M):
+    """Rational inverse by Gauss-Jordan elimination (independent of the
+    adjugate route the oracle takes)."""
+    d = len(M)
+    A = [[Fraction(x) for x in r] + [Fraction(int(i == j)) for j in range(d)] for i, r in enumerate(M)]
+    for c in range(d):
+        p = next(r for r in range(c, d) if A[r][c] != 0)
+        A[c], A[p] = A[p], A[c]
+        piv = A[c][c]
+        A[c] = [x / piv for x in A[c]]
+        for r in range(d):
+            if r != c and A[r][c] != 0:
+                f = A[r][c]
+                A[r] = [A[r][k] - f * A[c][k] for k in range(2 * d)]
+    return [r[d:] for r in A]
+
+
+def _box(M):
+    return list(itertools.product(*[range(n) for n in L.box_shape(M)]))
+
+
+# ---------------------------------------------------------------- transform
+@pytest.mark.parametrize("shape", [(12,), (4, 8), (6, 10), (2, 3, 5), (8, 4, 2)])
+def test_diagonal_matrix_gives_textbook_dft(shape):
+    """M = diag(n_1..n_d): eq. (Fouriermatrix) reduces to the d-dimensional DFT."""
+    M = [[shape[i] if i == j else 0 for j in range(len(shape))] for i in range(len(shape))]
+    m = int(np.prod(shape))
+    c = _rand_c(m, 2, seed=7)
+    ref = np.fft.fftn(c.reshape((2,) + shape), axes=range(1, len(shape) + 1), norm="ortho")
+    got = oracle.pattern_fft(M, c)
+    assert np.allclose(got, ref.reshape(2, m), atol=1e-12)
+    back = np.fft.ifftn(ref, axes=range(1, len(shape) + 1), norm="ortho").reshape(2, m)
+    assert np.allclose(oracle.pattern_fft(M, ref.reshape(2, m), inverse=True), back, atol=1e-12)
+
+
+@pytest.mark.parametrize("M", [[[4, -3], [4, 5]], [[3, 1], [-2, 5]], [[2, 7], [1, 1]],
+                               [[0, 3], [2, 1]], [[2, 1, 0], [0, 3, 1], [1, 0, 2]],
+                               [[1, 2, 0], [-1, 1, 3], [2, 0, 1]]])
+def test_brute_force_exact_rational_phase(M):
+    """Direct sum with k^T M^{-1} y formed exactly in rationals (Gauss-Jordan)."""
+    Minv = _gauss_jordan_inverse(M)
+    m = abs(L.det(M))
+    ys = _box(M)
+    ks = _box(L.transpose(M))
+    assert len(ys) == len(ks) == m
+    c = _rand_c(m, seed=3)[0]
+    ref = np.zeros(m, complex)
+    for a, k in enumerate(ks):
+        acc = 0j
+        for b, y in enumerate(ys):
+            ph = sum(k[i] * Minv[i][j] * y[j] for i in range(len(k)) for j in range(len(k)))
+            frac = ph - math.floor(ph)
+            acc += c[b] * cmath.exp(-2j * math.pi * float(frac))
+        ref[a] = acc / math.sqrt(m)
+    assert np.allclose(oracle.pattern_fft(M, c), ref, atol=1e-12)
+    # inverse: sum over k with the conjugate phase, output on the G(M) box
+    back = np.zeros(m, complex)
+    for b, y in enumerate(ys):
+        acc = 0j
+        for a, k in enumerate(ks):
+            ph = sum(k[i] * Minv[i][j] * y[j] for i in range(len(k)) for j in range(len(k)))
+            acc += ref[a] * cmath.exp(2j * math.pi * float(ph - math.floor(ph)))
+        back[b] = acc / math.sqrt(m)
+    assert np.allclose(oracle.pattern_fft(M, ref, inverse=True), back, atol=1e-12)
+    assert np.allclose(back, c, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_parseval_and_inverse_identity(seed):
+    rng = np.random.default_rng(100 + seed)
+    d = 2 + seed % 2
+    M = SI.random_regular_matrix(rng, d, 6, 600)
+    m = abs(L.det(M))
+    c = _rand_c(m, 3, seed)
+    ch = oracle.pattern_fft(M, c)
+    assert np.allclose(np.linalg.norm(ch, axis=1), np.linalg.norm(c, axis=1), rtol=1e-13)
+    assert np.allclose(oracle.pattern_fft(M, ch, inverse=True), c, atol=1e-12)
+
+
+@pytest.mark.parametrize("M", [SI.M_SMALL_2D, [[6, 2], [-2, 6]], [[4, 0], [0, 2]],
+                               SI.M_AUTOGRAD_TINY, [[3, 1, 2], [0, 2, 1], [1, 0, 4]],
+                               [[8, 2], [2, -4]], [[8, 8], [-8, 8]]])
+def test_kronecker_form_in_smith_coordinates(M):
+    """Thm 1: in the orderings of eq. (orderings) the transform is the tensor
+    product of 1-D DFTs.  lambda = Q^{-1} y mod eps, mu = R^{-T} k mod eps."""
+    Q, E, R = L.snf(M)
+    d = len(M)
+    eps = [E[i][i] for i in range(d)]
+    m = abs(L.det(M))
+    Qi = [[int(x) for x in r] for r in L.inverse(Q)]
+    RiT = [[int(x) for x in r] for r in L.transpose(L.inverse(R))]
+    c = _rand_c(m, seed=11)[0]
+    X = np.zeros(eps, complex)
+    for s, y in enumerate(_box(M)):
+        lam = tuple(v % e for v, e in zip(L.matvec(Qi, list(y)), eps))
+        X[lam] = c[s]
+    Y = np.fft.fftn(X, norm="ortho")
+    ref = np.array([Y[tuple(v % e for v, e in zip(L.matvec(RiT, list(k)), eps))]
+                    for k in _box(L.transpose(M))])
+    assert np.allclose(oracle.pattern_fft(M, c), ref, atol=1e-12)
+
+
+def test_sampled_slots_match_full_output():
+    M = [[40, 7], [0, 36]]
+    m = abs(L.det(M))
+    c = _rand_c(m, 2, seed=5)
+    full = oracle.pattern_fft(M, c)
+    slots = SI.sample_slots(m, 97, seed=1)
+    assert np.allclose(oracle.pattern_fft(M, c, out_slots=slots), full[:, slots], atol=1e-13)
+
+
+# ------------------------------------------------------- lattice / SNF pins
+@pytest.mark.parametrize("seed", range(40))
+def test_smith_form_properties(seed):
+    rng = np.random.default_rng(seed)
+    d = 1 + seed % 4
+    M = SI.random_regular_matrix(rng, d, 9, 10**6)
+    Q, E, R = L.snf(M)
+    assert L.matmul(L.matmul(Q, E), R) == M
+    assert abs(L.det(Q)) == 1 and abs(L.det(R)) == 1
+    eps = [E[i][i] for i in range(d)]
+    assert all(E[i][j] == 0 for i in range(d) for j in range(d) if i != j)
+    assert all(e > 0 for e in eps)
+    assert all(eps[j + 1] % eps[j] == 0 for j in range(d - 1))
+    assert math.prod(eps) == abs(L.det(M))
+
+
+def test_table1_cycle_lengths():
+    rows = [list(map(int, l.split())) for l in open(os.path.join(GOLD, "table1_cycles.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 12
+    for i, *cycles in rows:
+        eps = L.elementary_divisors([[2048, i], [0, 2048]])
+        assert [e for e in eps if e > 1] == cycles
+
+
+def test_example1_smith_diagonal():
+    vals = {l.split()[0]: list(map(int, l.split()[1:])) for l in open(os.path.join(GOLD, "example1.txt"))
+            if l.strip() and not l.startswith("#")}
+    M = [vals["M"][:2], vals["M"][2:]]
+    F1 = [vals["F1"][:2], vals["F1"][2:]]
+    F2 = [vals["F2"][:2], vals["F2"][2:]]
+    assert L.matmul(F1, F2) == M
+    assert L.elementary_divisors(M) == vals["E"]
+
+
+@pytest.mark.parametrize("M", [SI.M_SMALL_2D, SI.M_BATCHED_2D, SI.M_AUTOGRAD_3D, [[4, -3], [4, 5]],
+                               [[3, 1, 2], [0, 2, 1], [1, 0, 4]]])
+def test_lemma1_biorthogonality(M):
+    """<h_j, y_i> = delta_ij / eps_i for h_j = R^T e_j and y_i = R^{-1} e_i / eps_i."""
+    Q, E, R = L.snf(M)
+    d = len(M)
+    Ri = L.inverse(R)
+    for i in range(d):
+        for j in range(d):
+            hj = [R[j][r] for r in range(d)]
+            yi = [Ri[r][i] / E[i][i] for r in range(d)]
+            ip = sum(a * b for a, b in zip(hj, yi))
+            assert ip == (Fraction(1, E[i][i]) if i == j else 0)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_hnf_box_is_complete_residue_system(seed):
+    rng = np.random.default_rng(50 + seed)
+    d = 1 + seed % 3
+    M = SI.random_regular_matrix(rng, d, 5, 200)
+    H = L.hnf(M)
+    U = L.matmul(L.inverse(M), H)
+    assert all(x.denominator == 1 for r in U for x in r) and abs(L.det([[int(x) for x in r] for r in U])) == 1
+    assert all(H[r][c] == 0 for r in range(d) for c in range(r))
+    assert all(0 <= H[r][c] < H[r][r] for r in range(d) for c in range(r + 1, d))
+    Minv = L.inverse(M)
+    pts = _box(M)
+    assert len(pts) == abs(L.det(M))
+    keys = set()
+    for y in pts:  # class key: fractional part of M^{-1} y
+        t = L.matvec(Minv, list(y))
+        keys.add(tuple(x - math.floor(x) for x in t))
+    assert len(keys) == len(pts)
+    for y in [(5, -3, 7)[:d], (-11, 4, 2)[:d]]:
+        z = L.box_reduce(H, y)
+        diff = L.matvec(Minv, [a - b for a, b in zip(y, z)])
+        assert all(x.denominator == 1 for x in diff)
+
+
+# --------------------------------------------------------- wavelet pins
+def _closed_cube_reps(M, bound=None):
+    """All k in Z^d with M^{-T} k in [-1/2, 1/2]^d."""
+    MT = L.transpose(M)
+    MiT = L.inverse(MT)
+    d = len(M)
+    bound = bound or sum(abs(x) for r in M for x in r)
+    out = []
+    for k in itertools.product(range(-bound, bound + 1), repeat=d):
+        t = L.matvec(MiT, list(k))
+        if all(abs(x) <= Fraction(1, 2) for x in t):
+            out.append(k)
+    return out
+
+
+def _dirichlet_coeff(M, k):
+    """c_k(phi_M) of the Dirichlet kernel (Section 6.2)."""
+    t = L.matvec(L.inverse(L.transpose(M)), list(k))
+    if any(abs(x) > Fraction(1, 2) for x in t):
+        return 0.0
+    r = sum(abs(x) == Fraction(1, 2) for x in t)
+    return 2.0 ** (-r / 2) / math.sqrt(abs(L.det(M)))
+
+
+CASES = [([[8, 8], [-8, 8]], SI.J_DIAG_A), ([[8, 0], [0, 8]], SI.J_DIAG_B),
+         ([[8, 0], [0, 8]], [[2, 0], [0, 1]]), ([[8, 0], [0, 8]], [[1, 0], [0, 2]]),
+         ([[6, 2], [-2, 6]], SI.J_DIAG_A), ([[4, 4], [-4, 4]], SI.J_DIAG_A),
+         ([[4, 1, 0], [0, 4, 1], [0, 0, 4]], [[1, 0, 0], [0, 1, 0], [0, 0, 2]])]
+
+
+@pytest.mark.parametrize("M,J", CASES)
+def test_dirichlet_kernel_class_norm(M, J):
+    """Orthonormal translates of phi_M: the |c_k|^2 of each class of
+    G(M^T) add up to 1/m (the boundary weights 2^{-r} make this exact)."""
+    m = abs(L.det(M))
+    G = L.hnf(L.transpose(M))
+    acc = {}
+    for k in _closed_cube_reps(M):
+        key = L.box_reduce(G, k)
+        acc[key] = acc.get(key, 0.0) + _dirichlet_coeff(M, k) ** 2
+    assert len(acc) == m
+    assert all(abs(v - 1.0 / m) < 1e-14 for v in acc.values())
+
+
+@pytest.mark.parametrize("M,J", CASES)
+def test_dirichlet_two_scale_relation(M, J):
+    """c_k(phi_N) = A_h c_k(phi_M) for every k with M^{-T}k in the closed cube
+    (Section 6.2), with A from the oracle's scaling symbol."""
+    N = oracle.exact_N(M, J)
+    ks = _closed_cube_reps(M)
+    A = oracle.scaling_symbol(M, J, np.array(ks), oracle.DIRICHLET)
+    for k, a in zip(ks, A):
+        assert abs(_dirichlet_coeff(N, k) - a * _dirichlet_coeff(M, k)) < 1e-14
+
+
+def _split_roundtrip(M, J, symbol, eta, batch=2, seed=0):
+    m = abs(L.det(M))
+    c = _rand_c(m, batch, seed)
+    d1, d2 = oracle.wavelet_level(M, J, symbol, eta, c_hat=c)
+    back = oracle.wavelet_level(M, J, symbol, eta, d1=d1, d2=d2, mode="reconstruct")
+    return c, d1, d2, back
+
+
+@pytest.mark.parametrize("M,J", CASES)
+@pytest.mark.parametrize("symbol", [oracle.DIRICHLET, oracle.DLVP])
+def test_split_perfect_reconstruction(M, J, symbol):
+    c, d1, d2, back = _split_roundtrip(M, J, symbol, 0.125)
+    assert np.allclose(back, c, atol=1e-12)
+
+
+@pytest.mark.parametrize("M,J", CASES)
+def test_dirichlet_split_is_orthogonal(M, J):
+    c, d1, d2, back = _split_roundtrip(M, J, oracle.DIRICHLET, 0.0)
+    # norm preservation
+    assert np.allclose(np.linalg.norm(d1, axis=1) ** 2 + np.linalg.norm(d2, axis=1) ** 2,
+                       np.linalg.norm(c, axis=1) ** 2, rtol=1e-13)
+    # V_N^{phi_N} and V_N^{psi_N} are orthogonal: synthesised parts are orthogonal
+    z = np.zeros_like(d1)
+    v = oracle.wavelet_level(M, J, oracle.DIRICHLET, d1=d1, d2=z, mode="reconstruct")
+    w = oracle.wavelet_level(M, J, oracle.DIRICHLET, d1=z, d2=d2, mode="reconstruct")
+    assert abs(np.vdot(v, w)) < 1e-12 * np.linalg.norm(c) ** 2
+    assert np.allclose(v + w, c, atol=1e-12)
+
+
+@pytest.mark.parametrize("M,J", CASES[:4])
+@pytest.mark.parametrize("symbol", [oracle.DIRICHLET, oracle.DLVP])
+def test_split_adjoint_dot_product(M, J, symbol):
+    m = abs(L.det(M))
+    c = _rand_c(m, 1, 1)
+    e1 = _rand_c(m // 2, 1, 2)
+    e2 = _rand_c(m // 2, 1, 3)
+    d1, d2 = oracle.wavelet_level(M, J, symbol, 0.125, c_hat=c)
+    ct = oracle.wavelet_level(M, J, symbol, 0.125, d1=e1, d2=e2, mode="adjoint")
+    assert abs(np.vdot(e1, d1) + np.vdot(e2, d2) - np.vdot(ct, c)) < 1e-12 * m
+
+
+@pytest.mark.parametrize("M,J", CASES)
+def test_dlvp_partition_of_unity_and_dirichlet_limit(M, J):
+    """w(N^{-T} h0) + w(N^{-T} h1) = 1 on every fibre; as eta -> 0 the symbol
+    equals the Dirichlet one wherever the fibre has no boundary point."""
+    N = oracle.exact_N(M, J)
+    HN = L.hnf(L.transpose(N))
+    HM = L.hnf(L.transpose(M))
+    l1 = oracle.nonzero_class_JT(J)
+    NTl1 = L.matvec(L.transpose(N), l1)
+    hs0, hs1 = [], []
+    for g in L.box_points(HN):
+        hs0.append(L.box_reduce(HM, g))
+        hs1.append(L.box_reduce(HM, [a + b for a, b in zip(g, NTl1)]))
+    r2 = math.sqrt(abs(L.det(J)))
+    for eta in (0.125, 0.3):
+        w0 = oracle.scaling_symbol(M, J, np.array(hs0), oracle.DLVP, eta) / r2
+        w1 = oracle.scaling_symbol(M, J, np.array(hs1), oracle.DLVP, eta) / r2
+        assert np.allclose(w0 + w1, 1.0, atol=1e-14)
+        assert (w0 >= 0).all() and (w1 >= 0).all()
+    tiny = 1e-9
+    a0 = oracle.scaling_symbol(M, J, np.array(hs0), oracle.DLVP, tiny)
+    a1 = oracle.scaling_symbol(M, J, np.array(hs1), oracle.DLVP, tiny)
+    D0 = oracle.scaling_symbol(M, J, np.array(hs0), oracle.DIRICHLET)
+    D1 = oracle.scaling_symbol(M, J, np.array(hs1), oracle.DIRICHLET)
+    clean = (np.isin(D0, [0.0, math.sqrt(2)])) & (np.isin(D1, [0.0, math.sqrt(2)]))
+    assert clean.sum() > 0
+    assert np.allclose(a0[clean], D0[clean], atol=1e-6) and np.allclose(a1[clean], D1[clean], atol=1e-6)
+
+
+@pytest.mark.parametrize("symbol", [oracle.DIRICHLET, oracle.DLVP])
+def test_twelve_level_cascade_reconstructs(symbol):
+    M0 = [[64, 64], [-64, 64]]  # same shape family as the measured workload, det 2^13
+    Js = SI.wavelet_dilations(12)
+    m = abs(L.det(M0))
+    c = _rand_c(m, 2, 9)
+    s, w = oracle.wavelet_cascade(M0, Js, c, symbol, 0.125)
+    assert s.shape[1] == 2 and [x.shape[1] for x in w] == [m >> (l + 1) for l in range(12)]
+    back = oracle.wavelet_cascade_inverse(M0, Js, s, w, symbol, 0.125)
+    assert np.allclose(back, c, atol=1e-11)
+    if symbol == oracle.DIRICHLET:
+        tot = np.linalg.norm(s) ** 2 + sum(np.linalg.norm(x) ** 2 for x in w)
+        assert abs(tot - np.linalg.norm(c) ** 2) < 1e-10 * tot
+
+
+def test_cascade_matrices_follow_the_dilation_chain():
+    """N_{2k-1} = 2^{11-k} I and N_{2k} = 2^{10-k} [[1,1],[-1,1]] for the 12-level workload."""
+    M = SI.M_WAVELET_2D
+    for lev, J in enumerate(SI.wavelet_dilations(12), start=1):
+        M = oracle.exact_N(M, J)
+        k = (lev + 1) // 2
+        if lev % 2:
+            assert M == [[2 ** (11 - k), 0], [0, 2 ** (11 - k)]]
+        else:
+            s = 2 ** (10 - k)
+            assert M == [[s, s], [-s, s]]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_theorem3_dimension_step(seed):
+    """For |det J| = 2 (d_J = 1) the number of cycles grows by 0 or 1."""
+    rng = np.random.default_rng(seed)
+    J = [SI.J_DIAG_A, SI.J_DIAG_B, [[2, 0], [0, 1]], [[1, 0], [0, 2]]][seed % 4]
+    N = SI.random_regular_matrix(rng, 2, 7, 400)
+    M = L.matmul(J, N)
+    dM = sum(e > 1 for e in L.elementary_divisors(M))
+    dN = sum(e > 1 for e in L.elementary_divisors(N))
+    assert dM - dN in (0, 1)
