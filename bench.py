@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Benchmark of the pattern FFT hot path on GB300.
+
+A step is one forward and one inverse pattern FFT (both passes of each, with
+the gather / scatter between the Hermite boxes and the Smith coordinates
+fused in) over one batch of the batched 2-D workload: M = [[4096, 1024],
+[0, 4096]] (|det M| = 2^24, cycles (1024, 16384)), batch 8, complex64 inputs
+with i.i.d. N(0,1) parts, resident in HBM.  Each buffer is 1 GiB, larger than
+the 126 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+The value is transform points per second (each forward or inverse transform
+of m points counts m points) summed over all GPUs; for N > 1 every GPU runs
+an independent replica (the workload has no exchange step) and the time is
+the maximum over ranks.  One JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import seeded_inputs as SI  # noqa: E402
+
+METRIC = "pattern-FFT points/s & % of HBM roofline vs plain FP32 form at rel-L2≤1e-5"
+WORKLOAD = "batched_2d"
+BYTES_PER_POINT_PASS = 16  # complex64: 8 B read + 8 B write per point and pass
+KERNELS = ("row_pass", "col_pass")
+
+
+def workload_desc():
+    w = SI.WORKLOADS[WORKLOAD]
+    return {"workload": "batched 2-D pattern FFT, forward + inverse", "M": w["M"], "m": 1 << 24,
+            "batch": w["batch"], "cycles": [1024, 16384], "input": "complex64, re/im i.i.d. N(0,1), seed 1",
+            "l2": "inputs larger than L2 (1 GiB per buffer), no flush"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1107_5415_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(kernel)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def aggregate(ms_local: float, points_local: float, world: int):
+    """Whole-job numbers: time = max over ranks, points = sum over ranks."""
+    if world == 1:
+        return ms_local, points_local
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+    p = torch.tensor([points_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_sample_rate(target_s: float, threads: int | None = None):
+    """Oracle (direct FP64 sum) on a bounded sample of the workload: S output
+    frequencies of one signal.  Returns (points/s, seconds, S, threads)."""
+    import oracle
+    w = SI.WORKLOADS[WORKLOAD]
+    M = w["M"]
+    m = 1 << 24
+    c = SI.complex_normal(1, m, w["seed"], dtype=np.complex128)
+    nthreads = threads or os.cpu_count() or 1
+    probe = SI.sample_slots(m, max(2 * nthreads, 16), seed=3)
+    t0 = time.perf_counter()
+    oracle.pattern_fft(M, c, out_slots=probe, nthreads=nthreads)
+    per = (time.perf_counter() - t0) / len(probe)
+    S = int(max(len(probe), min(1 << 16, target_s / max(per, 1e-9))))
+    S = max(nthreads, (S // nthreads) * nthreads)
+    slots = SI.sample_slots(m, S, seed=5)
+    t0 = time.perf_counter()
+    oracle.pattern_fft(M, c, out_slots=slots, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return S / dt, dt, S, nthreads
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    target = float(os.environ.get("PFFT_REF_STEP_S", "2.0"))
+    times, rates = [], []
+    S = threads = None
+    for i in range(args.warmup + args.steps):
+        rate, dt, S, threads = oracle_sample_rate(target)
+        if i >= args.warmup:
+            times.append(dt)
+            rates.append(rate)
+    value = float(np.median(rates))
+    sample = (f"direct FP64 sum (oracle) for {S} seeded output frequencies of one of the 8 signals "
+              f"of the workload, per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.median(times)) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_desc(),
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args):
+    import torch
+    import paper_1107_5415_gb300 as pf
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = SI.WORKLOADS[WORKLOAD]
+    M, batch = w["M"], w["batch"]
+    plan = pf.PatternFFT(M, batch)
+    m = plan.m
+    host = torch.from_numpy(SI.complex_normal(batch, m, w["seed"] + 1000 * rank))
+    x = host.to(dev)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.forward(x, y)
+        plan.inverse(y, z)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    plan.profile(True)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    prof = plan.profile_read()
+    plan.profile(False)
+    barrier(world)
+    torch.cuda.synchronize()
+    points_local = 2.0 * m * batch  # forward + inverse transform points per step
+    ms_max, points = aggregate(ms, points_local, world)
+    value = points / (ms_max * 1e-3)
+
+    # end to end through the public API with host buffers (pinned), per step:
+    # H2D of the input, forward + inverse, D2H of the result
+    hin = host.pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        x.copy_(hin, non_blocking=True)
+        step()
+        hout.copy_(z, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        x.copy_(hin, non_blocking=True)
+        step()
+        hout.copy_(z, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms, _ = aggregate(e0.elapsed_time(e1) / e2e_steps, points_local, world)
+    e2e_value = points / (e2e_ms * 1e-3)
+
+    # roofline of the dominant kernel: algorithmic bytes per launch / mean duration
+    peaks, peak_kind = measured_peaks()
+    dom = max(KERNELS, key=lambda k: prof.get(k, (0, 0.0))[1])
+    launches, tot_ms = prof[dom]
+    avg_s = tot_ms / launches * 1e-3
+    alg_bytes = BYTES_PER_POINT_PASS * m * batch
+    achieved = alg_bytes / avg_s / 1e9
+    peak = float(peaks["hbm_gbs"])
+    traffic = recorded_traffic(dom)
+    kernels = {k: {"launches": int(v[0]), "avg_ms": v[1] / max(v[0], 1),
+                   "achieved_gbs": BYTES_PER_POINT_PASS * m * batch / (v[1] / max(v[0], 1) * 1e-3) / 1e9}
+               for k, v in prof.items() if v[0]}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            rate, dt, S, threads = oracle_sample_rate(float(os.environ.get("PFFT_CPU_BASELINE_S", "15")))
+            cpu = {"value": rate, "unit": "points/s", "cores": threads, "kind": "oracle",
+                   "sample": f"direct FP64 sum for {S} seeded output frequencies of one signal "
+                             f"({dt:.1f} s on the host cores)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_desc(),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_launch": alg_bytes},
+            "compulsory_frac": (BYTES_PER_POINT_PASS * points_local / (ms * 1e-3) / 1e9) / peak,
+            "kernels": kernels,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": int(x.numel() * 8),
+                    "d2h_bytes_per_step": int(z.numel() * 8)},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clk.summary(),
+            "impl": "native",
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    return run_reference(args) if args.impl == "reference" else run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * pfft.h -- C ABI of the GB300 pattern FFT / fast wavelet split library.
+ *
+ * The library computes the Fourier transform on the pattern P(M) of a regular
+ * integer matrix M (eq. (Fouriermatrix), Section 2.2),
+ *
+ *     c_hat[k] = m^{-1/2} sum_{y in G(M)} c[y] exp(-2 pi i k^T M^{-1} y),  k in G(M^T),
+ *
+ * m = |det M|, through the Kronecker factorisation in Smith coordinates
+ * (Theorem 1, Section 4.1; eq. (KroneckerFFT), Section 4.2), and the fast
+ * wavelet decomposition step built on it (Section 5.3, step 4): the split of
+ * Fourier coefficients on G(M^T) into scaling and wavelet parts on G(N^T),
+ * M = J N, |det J| = 2, with the Dirichlet symbols of Section 6.2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Layout ("box layout").  For an integer matrix A let H(A) be its column-style
+ *  Hermite normal form (H = A U, U unimodular, H upper triangular, H_rr > 0,
+ *  0 <= H_rc < H_rr for c > r; the pattern normal form of Section 6.1).  The
+ *  integer box  x_r [0, H_rr)  is a complete residue system of Z^d / A Z^d.
+ *  A signal on G(M) (equivalently on the pattern points M^{-1} y of P(M)) is
+ *  stored with y in the box of H(M); Fourier coefficients on G(M^T) are
+ *  stored with k in the box of H(M^T).  Slots are numbered row-major over the
+ *  box (last coordinate fastest).  pfft_index_map returns the coordinates.
+ *
+ *  Data.  Complex interleaved (re, im): PFFT_C64 = 2 x float, PFFT_C128 =
+ *  2 x double.  Buffers are DEVICE pointers owned by the caller, contiguous,
+ *  batch outermost ([batch][m]).  All transform calls are asynchronous and
+ *  stream-ordered on the given cudaStream_t (passed as void*, NULL = legacy
+ *  default stream); nothing on the hot path synchronises with the host.
+ *  Input and output must not overlap.
+ *
+ *  Ownership.  Plans own their device tables and workspace, released by the
+ *  matching *_destroy.  A plan may be used from one stream at a time (the
+ *  workspace is shared by all calls on the plan).
+ *
+ *  Errors.  Every entry point returns a pfft_status.  Argument, planning and
+ *  capacity errors are detected on the host and returned synchronously before
+ *  any work is queued.  Errors raised by the CUDA runtime while queueing are
+ *  returned as PFFT_ERR_CUDA.  There is no CPU fallback: without a usable GPU
+ *  the plan constructors return PFFT_ERR_CUDA.
+ *
+ *  Limits.  1 <= d <= 4, |M_ij| < 2^24, 1 <= |det M| < 2^31.  The transform
+ *  kernels handle at most three non-trivial Smith cycles; the longest cycle
+ *  (the last elementary divisor eps_d) must fit one shared-memory tile
+ *  (eps_d <= 16384 for PFFT_C64, <= 8192 for PFFT_C128), and so must the
+ *  product of the other cycles.  Cycle lengths may contain the prime factors
+ *  2, 3, 5, 7, 11, 13, 17, 19, 23, 29 and 31.  Anything else is rejected with
+ *  PFFT_ERR_UNSUPPORTED at plan time.
+ */
+#ifndef PFFT_H
+#define PFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pfft_plan_s* pfft_plan;
+typedef struct pwt_plan_s* pwt_plan;
+
+typedef enum {
+  PFFT_OK = 0,
+  PFFT_ERR_ARG = 1,          /* NULL pointer, bad d / batch / dtype / flag / level */
+  PFFT_ERR_SINGULAR = 2,     /* det M == 0 (or det J == 0) */
+  PFFT_ERR_OVERFLOW = 3,     /* entries or determinant beyond the stated limits */
+  PFFT_ERR_NOT_INTEGRAL = 4, /* J^{-1} M is not an integer matrix */
+  PFFT_ERR_UNSUPPORTED = 5,  /* valid input outside what the kernels handle */
+  PFFT_ERR_OOM = 6,          /* device allocation failed */
+  PFFT_ERR_CUDA = 7,         /* CUDA runtime error (incl. no device) */
+  PFFT_ERR_TIMEOUT = 8,      /* reserved: a bounded device wait gave up */
+  PFFT_ERR_DEVICE_CHECK = 9  /* reserved: a device-side check failed */
+} pfft_status;
+
+enum { PFFT_C64 = 0, PFFT_C128 = 1 };
+
+/* Which index map pfft_index_map returns. */
+enum {
+  PFFT_MAP_INPUT_BOX = 0,   /* per input slot: y (d coordinates) in the box of H(M)     */
+  PFFT_MAP_OUTPUT_BOX = 1,  /* per output slot: k (d coordinates) in the box of H(M^T)  */
+  PFFT_MAP_INPUT_SNF = 2,   /* per input slot: Smith coordinates lambda (d_M values)    */
+  PFFT_MAP_OUTPUT_SNF = 3   /* per output slot: Smith coordinates mu (d_M values)       */
+};
+
+/* Human-readable name of a status code (static string). */
+const char* pfft_status_string(pfft_status s);
+
+/* ---------------------------------------------------------------------------
+ * Host-only planner queries (exact integer arithmetic, no GPU needed).
+ * ------------------------------------------------------------------------- */
+
+/* Hermite normal form H of the d x d row-major integer matrix M (Section 6.1,
+ * eq. (FFTexampleMatrix): the upper-triangular normal form of a pattern).
+ * H (d*d, row-major) is written by the callee; caller-owned host memory. */
+pfft_status pfft_hermite_normal_form(int d, const int64_t* M, int64_t* H);
+
+/* Smith normal form M = Q E R (eq. (SNF), Section 2.2): Q, R unimodular,
+ * E = diag(eps), eps_j | eps_{j+1}.  Q, R: d*d row-major; eps: d values.
+ * Host memory owned by the caller. */
+pfft_status pfft_smith_normal_form(int d, const int64_t* M, int64_t* Q, int64_t* eps, int64_t* R);
+
+/* ---------------------------------------------------------------------------
+ * Pattern FFT plans.
+ * ------------------------------------------------------------------------- */
+
+/* Plan the transform on P(M) for `batch` signals of |det M| points each.
+ * M: d*d row-major host array.  dtype: PFFT_C64 or PFFT_C128.  flags: 0.
+ * Computes H(M), H(M^T), the Smith form and the basis of Theorem 1
+ * (Section 3, eqs. (basisPM), (basisGM); Remark 2 allows any biorthogonal
+ * pair, and the planner picks the one whose longest cycle runs along the
+ * fastest input coordinate), uploads the index tables, builds the twiddle
+ * table on the device (exact integer phase, FP64 sincospi, rounded to the
+ * working precision) and allocates the workspace (|det M| * batch complex
+ * values).  Synchronises the current device once (setup only). */
+pfft_status pfft_plan_create(pfft_plan* out, int d, const int64_t* M, int64_t batch, int dtype,
+                             unsigned flags);
+
+/* Sizes of a plan.  Any output pointer may be NULL.
+ *   m       : |det M|
+ *   dM      : number of Smith cycles longer than one (d_M of Section 2.2)
+ *   eps     : d elementary divisors, ascending
+ *   in_box  : d extents of the input box (diagonal of H(M))
+ *   out_box : d extents of the output box (diagonal of H(M^T)) */
+pfft_status pfft_plan_info(pfft_plan p, int64_t* m, int* dM, int64_t* eps, int64_t* in_box,
+                           int64_t* out_box);
+
+/* Host copy of an index map (see PFFT_MAP_*).  coords: caller-owned host
+ * array of m*d int64 (box maps) or m*dM int64 (Smith maps), slot-major. */
+pfft_status pfft_index_map(pfft_plan p, int which, int64_t* coords);
+
+/* The same maps as the device kernels evaluate them: for every Smith
+ * coordinate vector (row-major over the non-trivial cycles) the box slot the
+ * kernels read (which = PFFT_MAP_INPUT_BOX) or write (PFFT_MAP_OUTPUT_BOX).
+ * slots: caller-owned DEVICE array of m int64.  Asynchronous on `stream`. */
+pfft_status pfft_device_index_map(pfft_plan p, int which, int64_t* slots, void* stream);
+
+/* Forward transform (eq. (Fouriermatrix)): in on the box of H(M), out on the
+ * box of H(M^T), both [batch][m] complex device arrays; unitary scaling. */
+pfft_status pfft_forward(pfft_plan p, const void* in, void* out, void* stream);
+
+/* Inverse transform = adjoint (F(M) is unitary): in on the box of H(M^T),
+ * out on the box of H(M). */
+pfft_status pfft_inverse(pfft_plan p, const void* in, void* out, void* stream);
+
+pfft_status pfft_plan_destroy(pfft_plan p);
+
+/* Per-kernel timing of a plan's launches (CUDA events recorded on the
+ * launching stream around each kernel).  enable != 0 starts recording and
+ * clears the totals.  pfft_profile_read writes up to `cap` entries: kernel
+ * name (static string), launch count and summed milliseconds; it
+ * synchronises with the recorded events.  Returns the entry count in *n. */
+pfft_status pfft_profile_enable(pfft_plan p, int enable);
+pfft_status pfft_profile_read(pfft_plan p, const char** names, int64_t* launches, double* ms,
+                              int cap, int* n);
+
+/* ---------------------------------------------------------------------------
+ * Wavelet split plans (Section 5.3; Dirichlet symbols of Section 6.2).
+ * ------------------------------------------------------------------------- */
+
+enum { PWT_DIRICHLET = 0, PWT_DLVP = 1 };
+
+/* Plan `levels` split steps: level l (1-based) splits coefficients on
+ * G(M_l^T) (M_1 = M) into a scaling part and a wavelet part on G(N_l^T),
+ * N_l = J_l^{-1} M_l, and level l+1 splits the scaling part (M_{l+1} = N_l).
+ *   J      : levels*d*d row-major host array of dilations, |det J_l| = 2
+ *   symbol : PWT_DIRICHLET (Section 6.2) or PWT_DLVP (de la Vallee Poussin
+ *            reading: sqrt|det J| times the periodised trapezoid of blend
+ *            width eta, 0 < eta < 1; not defined in the paper)
+ *   batch, dtype as for pfft_plan_create; flags: 0.
+ * Returns PFFT_ERR_NOT_INTEGRAL if some J_l^{-1} M_l is not integral. */
+pfft_status pwt_plan_create(pwt_plan* out, int d, const int64_t* M, int levels, const int64_t* J,
+                            int symbol, double eta, int64_t batch, int dtype, unsigned flags);
+
+/* Size and output box of level l (1 <= l <= levels): n_l = |det N_l| and the
+ * d extents of the box of H(N_l^T).  Level 0 returns the input (M_1). */
+pfft_status pwt_plan_info(pwt_plan p, int level, int64_t* n, int64_t* box);
+
+/* Decompose: c_hat [batch][|det M|] on G(M^T)  ->  wavelets[l-1] [batch][n_l]
+ * on G(N_l^T) for every level and scaling [batch][n_levels] on
+ * G(N_levels^T).  Per level and fibre {h0, h1} of g in G(N^T):
+ *   d1[g] = 2^{-1/2} (conj A(h0) c[h0] + conj A(h1) c[h1])
+ *   d2[g] = 2^{-1/2} (conj B(h0) c[h0] + conj B(h1) c[h1]),
+ * B(h) = A(h + N^T l) exp(-2 pi i h^T N^{-1} z) (Section 6.2), z the non-zero
+ * element of Lambda(J) cap [-1/2, 1/2)^d.  Device pointers; `wavelets` is a
+ * HOST array of `levels` device pointers. */
+pfft_status pwt_decompose(pwt_plan p, const void* c_hat, void* scaling, void* const* wavelets,
+                          void* stream);
+
+/* Exact inverse of pwt_decompose (perfect reconstruction): per fibre
+ * c[h] = sqrt(2) (A(h) d1[g] + B(h) d2[g]) / (|A(h0)|^2 + |A(h1)|^2). */
+pfft_status pwt_reconstruct(pwt_plan p, const void* scaling, const void* const* wavelets,
+                            void* c_hat, void* stream);
+
+/* Adjoint (conjugate transpose) of pwt_decompose: c[h] = 2^{-1/2} (A d1 + B d2)
+ * per level; equals pwt_reconstruct for the Dirichlet symbol. */
+pfft_status pwt_adjoint(pwt_plan p, const void* scaling, const void* const* wavelets, void* c_hat,
+                        void* stream);
+
+pfft_status pwt_plan_destroy(pwt_plan p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFFT_H */

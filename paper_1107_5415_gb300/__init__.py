@@ -1,0 +1,233 @@
+"""GB300 pattern FFT and fast wavelet split (sm_103a).
+
+The Fourier transform on the pattern P(M) of a regular integer matrix M
+(eq. (Fouriermatrix), Section 2.2) and the wavelet split step built on it
+(Section 5.3, step 4; Dirichlet symbols of Section 6.2), computed by
+hand-written CUDA kernels behind the C ABI of ``include/pfft.h``.
+
+PyTorch supplies device memory, streams and autograd only; every step of the
+transform runs in the library's kernels.  If the library cannot be loaded,
+every operation raises -- there is no CPU fallback.
+
+Layout: a signal on P(M) is a complex tensor ``[batch, m]`` whose slot s holds
+the value at y = box point s of the Hermite normal form H(M) (row-major, last
+coordinate fastest); Fourier coefficients are stored the same way over the box
+of H(M^T).  ``PatternFFT.index_map`` returns those coordinates.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _capi
+from ._capi import (PFFT_C64, PFFT_C128, PFFT_MAP_INPUT_BOX, PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_BOX,
+                    PFFT_MAP_OUTPUT_SNF, PWT_DIRICHLET, PWT_DLVP, PfftError, pfft_device_index_map,
+                    pfft_forward, pfft_hermite_normal_form, pfft_index_map, pfft_inverse, pfft_plan_create,
+                    pfft_plan_destroy, pfft_plan_info, pfft_profile_enable, pfft_profile_read,
+                    pfft_smith_normal_form, pwt_adjoint, pwt_decompose, pwt_plan_create, pwt_plan_destroy,
+                    pwt_plan_info, pwt_reconstruct)
+
+__all__ = [
+    "PatternFFT", "WaveletSplit", "pattern_fft", "pattern_ifft", "wavelet_decompose",
+    "PfftError", "PFFT_C64", "PFFT_C128", "PWT_DIRICHLET", "PWT_DLVP",
+    "PFFT_MAP_INPUT_BOX", "PFFT_MAP_OUTPUT_BOX", "PFFT_MAP_INPUT_SNF", "PFFT_MAP_OUTPUT_SNF",
+    "pfft_plan_create", "pfft_plan_info", "pfft_index_map", "pfft_device_index_map", "pfft_forward",
+    "pfft_inverse", "pfft_plan_destroy", "pfft_profile_enable", "pfft_profile_read",
+    "pfft_hermite_normal_form", "pfft_smith_normal_form", "pwt_plan_create", "pwt_plan_info",
+    "pwt_decompose", "pwt_reconstruct", "pwt_adjoint", "pwt_plan_destroy", "library_path",
+]
+
+
+def library_path() -> str:
+    """Path of the loaded shared library (building it first if needed)."""
+    _capi.lib()
+    return _capi.build_lib.LIB
+
+
+def _dtype_code(dtype) -> int:
+    if dtype == torch.complex64:
+        return PFFT_C64
+    if dtype == torch.complex128:
+        return PFFT_C128
+    raise ValueError("dtype must be torch.complex64 or torch.complex128")
+
+
+def _stream(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _check_tensor(x: torch.Tensor, dtype, shape, name: str):
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if x.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}")
+    if tuple(x.shape) != tuple(shape) or not x.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous tensor of shape {tuple(shape)}")
+
+
+class PatternFFT:
+    """Plan of the transform on P(M) for ``batch`` signals (wraps pfft_plan)."""
+
+    def __init__(self, M, batch: int = 1, dtype=torch.complex64):
+        self.M = np.asarray(M, dtype=np.int64)
+        self.d = int(self.M.shape[0])
+        self.batch = int(batch)
+        self.dtype = dtype
+        self._h = pfft_plan_create(self.M, self.batch, _dtype_code(dtype))
+        self.m, self.dM, self.eps, self.in_box, self.out_box = pfft_plan_info(self._h, self.d)
+
+    @property
+    def shape(self):
+        return (self.batch, self.m)
+
+    def forward(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """c_hat = F(M) c: x on the box of H(M), result on the box of H(M^T)."""
+        _check_tensor(x, self.dtype, self.shape, "input")
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device=x.device)
+        _check_tensor(out, self.dtype, self.shape, "output")
+        pfft_forward(self._h, x.data_ptr(), out.data_ptr(), _stream(stream))
+        return out
+
+    def inverse(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """c = F(M)^H c_hat (F(M) is unitary)."""
+        _check_tensor(x, self.dtype, self.shape, "input")
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device=x.device)
+        _check_tensor(out, self.dtype, self.shape, "output")
+        pfft_inverse(self._h, x.data_ptr(), out.data_ptr(), _stream(stream))
+        return out
+
+    def index_map(self, which: int) -> np.ndarray:
+        width = self.d if which in (PFFT_MAP_INPUT_BOX, PFFT_MAP_OUTPUT_BOX) else max(self.dM, 1)
+        return pfft_index_map(self._h, which, self.m, width)
+
+    def device_index_map(self, which: int, device=None) -> torch.Tensor:
+        out = torch.empty(self.m, dtype=torch.int64, device=device or "cuda")
+        pfft_device_index_map(self._h, which, out.data_ptr(), _stream(None))
+        return out
+
+    def profile(self, enable: bool = True):
+        pfft_profile_enable(self._h, enable)
+
+    def profile_read(self):
+        return pfft_profile_read(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            pfft_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _FFTFn(torch.autograd.Function):
+    """y = F c with the hand-written adjoint: dL/dc = F^H dL/dy (= inverse)."""
+
+    @staticmethod
+    def forward(ctx, x, plan, inverse):
+        ctx.plan = plan
+        ctx.inverse = inverse
+        x = x.contiguous()
+        return plan.inverse(x) if inverse else plan.forward(x)
+
+    @staticmethod
+    def backward(ctx, g):
+        g = g.contiguous()
+        # F is unitary, so its adjoint is its inverse (and vice versa).
+        return (ctx.plan.forward(g) if ctx.inverse else ctx.plan.inverse(g)), None, None
+
+
+def pattern_fft(x: torch.Tensor, plan: PatternFFT) -> torch.Tensor:
+    """Differentiable forward transform."""
+    return _FFTFn.apply(x, plan, False)
+
+
+def pattern_ifft(x: torch.Tensor, plan: PatternFFT) -> torch.Tensor:
+    """Differentiable inverse transform."""
+    return _FFTFn.apply(x, plan, True)
+
+
+class WaveletSplit:
+    """Plan of ``levels`` split steps (wraps pwt_plan)."""
+
+    def __init__(self, M, Js, symbol: int = PWT_DIRICHLET, eta: float = 0.125, batch: int = 1,
+                 dtype=torch.complex64):
+        self.M = np.asarray(M, dtype=np.int64)
+        self.d = int(self.M.shape[0])
+        self.Js = np.asarray(Js, dtype=np.int64)
+        self.levels = int(self.Js.shape[0])
+        self.batch = int(batch)
+        self.dtype = dtype
+        self._h = pwt_plan_create(self.M, self.Js, symbol, eta, self.batch, _dtype_code(dtype))
+        self.sizes = []
+        self.boxes = []
+        for lev in range(self.levels + 1):
+            n, box = pwt_plan_info(self._h, lev, self.d)
+            self.sizes.append(n)
+            self.boxes.append(box)
+
+    def decompose(self, c_hat: torch.Tensor, stream=None):
+        """Returns (scaling [batch, n_L], [wavelet_l [batch, n_l] for l = 1..L])."""
+        _check_tensor(c_hat, self.dtype, (self.batch, self.sizes[0]), "c_hat")
+        dev = c_hat.device
+        wav = [torch.empty((self.batch, self.sizes[l + 1]), dtype=self.dtype, device=dev)
+               for l in range(self.levels)]
+        sc = torch.empty((self.batch, self.sizes[-1]), dtype=self.dtype, device=dev)
+        pwt_decompose(self._h, c_hat.data_ptr(), sc.data_ptr(), [w.data_ptr() for w in wav], _stream(stream))
+        return sc, wav
+
+    def _synth(self, fn, scaling, wavelets, stream):
+        _check_tensor(scaling, self.dtype, (self.batch, self.sizes[-1]), "scaling")
+        if len(wavelets) != self.levels:
+            raise ValueError("one wavelet part per level is required")
+        for l, w in enumerate(wavelets):
+            _check_tensor(w, self.dtype, (self.batch, self.sizes[l + 1]), f"wavelet[{l}]")
+        out = torch.empty((self.batch, self.sizes[0]), dtype=self.dtype, device=scaling.device)
+        fn(self._h, scaling.data_ptr(), [w.data_ptr() for w in wavelets], out.data_ptr(), _stream(stream))
+        return out
+
+    def reconstruct(self, scaling, wavelets, stream=None):
+        return self._synth(pwt_reconstruct, scaling, wavelets, stream)
+
+    def adjoint(self, scaling, wavelets, stream=None):
+        return self._synth(pwt_adjoint, scaling, wavelets, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            pwt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _SplitFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, c_hat, plan):
+        ctx.plan = plan
+        sc, wav = plan.decompose(c_hat.contiguous())
+        return (sc, *wav)
+
+    @staticmethod
+    def backward(ctx, g_sc, *g_wav):
+        plan = ctx.plan
+        z = lambda t, n: torch.zeros((plan.batch, n), dtype=plan.dtype, device="cuda") if t is None \
+            else t.contiguous()
+        g_sc = z(g_sc, plan.sizes[-1])
+        g_wav = [z(g, plan.sizes[l + 1]) for l, g in enumerate(g_wav)]
+        return plan.adjoint(g_sc, g_wav), None
+
+
+def wavelet_decompose(c_hat: torch.Tensor, plan: WaveletSplit):
+    """Differentiable multi-level split; backward runs the adjoint kernels."""
+    out = _SplitFn.apply(c_hat, plan)
+    return out[0], list(out[1:])

@@ -1,0 +1,563 @@
+// Host planner and C entry points for the pattern FFT (setup is host-side,
+// exact integers; every transform step runs in the kernels of fft_kernels.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pfft.h"
+#include "fft_plan.hpp"
+#include "lattice.hpp"
+#include "plan_common.hpp"
+
+using namespace pfft;
+
+struct pfft_plan_s {
+  int d = 0;
+  int64_t batch = 0;
+  int dtype = 0;
+  IMat M, H, G;
+  i64 m = 0;
+  std::vector<i64> eps;                 // all d elementary divisors
+  int D = 0;                            // non-trivial cycles
+  std::vector<int> n;                   // their lengths, ascending
+  std::vector<std::vector<i64>> LAM;    // D rows: lambda_j(y) = LAM_j . y mod n_j
+  std::vector<std::vector<i64>> MU;     // D rows: mu_j(k) = MU_j . k mod n_j
+  int nD = 1, LB = 1;
+  // device state
+  int device = 0;
+  int* dtab = nullptr;
+  void* tw = nullptr;
+  void* ws = nullptr;
+  PassArgs rowp{}, colp{};
+  Profiler prof;
+};
+
+namespace {
+
+// Radices for a cycle length: 16s first, then the rest of the power of two,
+// then odd primes.  Returns false if a prime factor is not supported.
+bool factor_radices(int n, std::vector<int>& out) {
+  out.clear();
+  int p2 = 0;
+  while (n % 2 == 0) {
+    n /= 2;
+    ++p2;
+  }
+  while (p2 >= 4) {
+    out.push_back(16);
+    p2 -= 4;
+  }
+  if (p2 == 3) out.push_back(8);
+  if (p2 == 2) out.push_back(4);
+  if (p2 == 1) out.push_back(2);
+  static const int primes[] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
+  for (int p : primes)
+    while (n % p == 0) {
+      out.push_back(p);
+      n /= p;
+    }
+  return n == 1;
+}
+
+void set_box(BoxDesc& B, const IMat& H) {
+  std::memset(&B, 0, sizeof(B));
+  B.d = H.d;
+  for (int i = 0; i < H.d; ++i)
+    for (int j = 0; j < H.d; ++j) B.H[i][j] = int(H(i, j));
+  int s = 1;
+  for (int r = H.d - 1; r >= 0; --r) {
+    B.stride[r] = s;
+    s *= int(H(r, r));
+  }
+}
+
+// Stages of a Stockham DFT along one pencil axis of length a and stride
+// sigma, in the radix order of kRadixOrder (Ns accumulates in that order).
+bool axis_stages(std::vector<StageDesc>& out, int a, int sigma, int nD) {
+  std::vector<int> rad;
+  if (!factor_radices(a, rad)) return false;
+  int Ns = 1;
+  for (int R : rad) {
+    StageDesc s;
+    std::memset(&s, 0, sizeof(s));
+    s.R = R;
+    s.a = a;
+    s.aR = a / R;
+    s.sigma = sigma;
+    s.Ns = Ns;
+    s.twstep = nD / (Ns * R);
+    s.div_aR.init(uint32_t(s.aR));
+    s.div_sigma.init(uint32_t(sigma));
+    s.div_Ns.init(uint32_t(Ns));
+    out.push_back(s);
+    Ns *= R;
+  }
+  return true;
+}
+
+int radix_region(int R) {
+  for (int i = 0; i < 14; ++i)
+    if (kRadixOrder[i] == R) return i;
+  return -1;
+}
+
+// Merge the stages of all axes, grouped by radix region (stable, so each
+// axis keeps its own order), and fill the per-region counts.
+bool set_stages(PassArgs& p, std::vector<StageDesc> all) {
+  std::stable_sort(all.begin(), all.end(), [](const StageDesc& x, const StageDesc& y) {
+    return radix_region(x.R) < radix_region(y.R);
+  });
+  if (all.size() > size_t(kMaxStages)) return false;
+  p.nstages = int(all.size());
+  std::memset(p.cnt, 0, sizeof(p.cnt));
+  p.pow2 = 1;
+  for (size_t i = 0; i < all.size(); ++i) {
+    const int reg = radix_region(all[i].R);
+    if (reg < 0) return false;
+    p.st[i] = all[i];
+    p.cnt[reg] += 1;
+    if (reg > 3) p.pow2 = 0;
+  }
+  return true;
+}
+
+// Threads needed so that every stage fits its per-thread register budget.
+int threads_for(const PassArgs& p, int ept) {
+  int need = (p.T * p.L + ept - 1) / ept;
+  for (int i = 0; i < p.nstages; ++i) {
+    const int R = p.st[i].R;
+    const int nb = std::max(1, ept / R);
+    const int bfly = p.T * p.L / R;
+    need = std::max(need, (bfly + nb - 1) / nb);
+  }
+  need = ((need + 31) / 32) * 32;
+  return need;
+}
+
+size_t elem_bytes(int dtype) { return dtype == PFFT_C64 ? 8 : 16; }
+
+pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) {
+  const int ept = P.dtype == PFFT_C64 ? 32 : 16;
+  p.cols = cols;
+  p.nD = P.nD;
+  p.LB = P.LB;
+  p.m = int(P.m);
+  p.d = P.d;
+  p.batch = int(P.batch);
+  p.T = T;
+  std::vector<StageDesc> stg;
+  if (!cols) {
+    p.L = P.nD;
+    if (!axis_stages(stg, P.nD, 1, P.nD)) return PFFT_ERR_UNSUPPORTED;
+    p.groups = (P.LB + T - 1) / T;
+  } else {
+    p.L = P.LB;
+    int sigma = 1;
+    for (int s = P.D - 2; s >= 0; --s) {  // pencil axes n_1..n_{D-1}, last fastest
+      if (!axis_stages(stg, P.n[s], sigma, P.nD)) return PFFT_ERR_UNSUPPORTED;
+      sigma *= P.n[s];
+    }
+    p.groups = P.nD / T;
+  }
+  if (!set_stages(p, stg)) return PFFT_ERR_UNSUPPORTED;
+  p.divT.init(uint32_t(T));
+  p.divnD.init(uint32_t(P.nD));
+  p.nthreads = threads_for(p, ept);
+  if (p.nthreads > kMaxThreads) return PFFT_ERR_UNSUPPORTED;
+  const int nel = T * p.L;
+  p.smem_bytes = int(size_t((nel - 1) + ((nel - 1) >> 4) + 1) * elem_bytes(P.dtype));
+  if (p.smem_bytes > 227 * 1024) return PFFT_ERR_UNSUPPORTED;
+  return PFFT_OK;
+}
+
+// Choose the pencils-per-CTA count: the largest power of two (<= cap) whose
+// tile fits `budget` elements and the thread limit.
+pfft_status choose_and_configure(PassArgs& p, const pfft_plan_s& P, bool cols, int cap, int budget) {
+  const int L = cols ? P.LB : P.nD;
+  const int limit = cols ? P.nD : P.LB;
+  int T = 1;
+  while (T * 2 <= cap && T * 2 <= limit && T * 2 * L <= budget && (!cols || P.nD % (T * 2) == 0)) T *= 2;
+  for (;;) {
+    pfft_status st = configure_pass(p, P, cols, T);
+    if (st == PFFT_OK) return st;
+    if (T == 1) return st;
+    T /= 2;
+  }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- planning
+static pfft_status plan_host(pfft_plan_s& P, int d, const int64_t* Mv) {
+  if (d < 1 || d > 4) return PFFT_ERR_ARG;
+  P.d = d;
+  P.M = IMat(d);
+  for (int i = 0; i < d * d; ++i) {
+    if (Mv[i] >= (int64_t(1) << 24) || Mv[i] <= -(int64_t(1) << 24)) return PFFT_ERR_OVERFLOW;
+    P.M.a[i] = Mv[i];
+  }
+  const i64 det = determinant(P.M);
+  if (det == 0) return PFFT_ERR_SINGULAR;
+  P.m = det < 0 ? -det : det;
+  if (P.m >= (i64(1) << 31)) return PFFT_ERR_OVERFLOW;
+  P.H = hermite_normal_form(P.M);
+  P.G = hermite_normal_form(P.M.transpose());
+  IMat Q, R, U, V;
+  smith_normal_form(P.M, Q, P.eps, R, U, V);
+  // lambda = Q^{-1} y = U y mod eps ;  mu = R^{-T} k = V^T k mod eps
+  std::vector<std::vector<i64>> LAM(d, std::vector<i64>(d)), MU(d, std::vector<i64>(d));
+  for (int j = 0; j < d; ++j)
+    for (int c = 0; c < d; ++c) {
+      LAM[j][c] = posmod(U(j, c), P.eps[j]);
+      MU[j][c] = posmod(V(c, j), P.eps[j]);
+    }
+  // Remark 2: any biorthogonal pair of bases works.  If the fastest input
+  // coordinate e_f generates a cycle of maximal length, re-base so that it is
+  // the generator of the last cycle; then the row pass reads contiguous runs.
+  {
+    const int f = d - 1;
+    const i64 E = P.eps[d - 1];
+    int j0 = -1;
+    for (int j = d - 1; j >= 0; --j)
+      if (P.eps[j] == E && gcd64(LAM[j][f], E) == 1) {
+        j0 = j;
+        break;
+      }
+    if (j0 >= 0 && E > 1) {
+      std::vector<i64> v(d);
+      for (int j = 0; j < d; ++j) v[j] = LAM[j][f] % P.eps[j];
+      const i64 u = modinv(v[j0], E);
+      auto L2 = LAM, M2 = MU;
+      for (int c = 0; c < d; ++c) L2[j0][c] = posmod(i64((i128)u * LAM[j0][c] % E), E);
+      for (int j = 0; j < d; ++j) {
+        if (j == j0) continue;
+        for (int c = 0; c < d; ++c) {
+          i128 t = (i128)LAM[j][c] - (i128)v[j] * u % P.eps[j] * LAM[j0][c];
+          L2[j][c] = posmod(i64(t % P.eps[j]), P.eps[j]);
+        }
+      }
+      for (int c = 0; c < d; ++c) {
+        i128 s = 0;
+        for (int i = 0; i < d; ++i) s += (i128)v[i] * (E / P.eps[i]) % E * MU[i][c];
+        M2[j0][c] = posmod(i64(s % E), E);
+      }
+      std::swap(L2[j0], L2[d - 1]);
+      std::swap(M2[j0], M2[d - 1]);
+      LAM = L2;
+      MU = M2;
+    }
+  }
+  P.D = 0;
+  P.n.clear();
+  P.LAM.clear();
+  P.MU.clear();
+  for (int j = 0; j < d; ++j)
+    if (P.eps[j] > 1) {
+      P.n.push_back(int(P.eps[j]));
+      P.LAM.push_back(LAM[j]);
+      P.MU.push_back(MU[j]);
+      ++P.D;
+    }
+  if (P.D > 3) return PFFT_ERR_UNSUPPORTED;
+  P.nD = P.D ? P.n[P.D - 1] : 1;
+  P.LB = int(P.m / P.nD);
+  return PFFT_OK;
+}
+
+namespace {
+// g_j = M MU_j^T / n_j  (in box(H));  h_j = M^T LAM_j^T / n_j  (in box(G)).
+std::vector<i64> generator(const IMat& A, const std::vector<i64>& row, i64 nj, const IMat& box) {
+  const int d = A.d;
+  std::vector<i64> g(d);
+  for (int i = 0; i < d; ++i) {
+    i128 s = 0;
+    for (int c = 0; c < d; ++c) s += (i128)A(i, c) * row[c];
+    if (s % nj != 0) throw LatticeError{PFFT_ERR_OVERFLOW, "generator is not integral"};
+    g[i] = i64(s / nj);
+  }
+  box_reduce(box, g.data());
+  return g;
+}
+
+std::vector<i64> combo(const std::vector<std::vector<i64>>& gens, const std::vector<i64>& coef,
+                       const IMat& box) {
+  const int d = box.d;
+  std::vector<i64> y(d, 0);
+  for (size_t j = 0; j < gens.size(); ++j)
+    for (int r = 0; r < d; ++r) y[r] += coef[j] * gens[j][r];  // < 2^62: coef, gens < 2^31
+  box_reduce(box, y.data());
+  return y;
+}
+}  // namespace
+
+static pfft_status plan_device(pfft_plan_s& P) {
+  const int d = P.d, D = P.D;
+  if (cudaGetDevice(&P.device) != cudaSuccess) return PFFT_ERR_CUDA;
+  if (D == 0) return PFFT_OK;  // m == 1: the transform is the identity
+  // generators of the cycles
+  std::vector<std::vector<i64>> g(D), h(D);
+  for (int j = 0; j < D; ++j) {
+    g[j] = generator(P.M, P.MU[j], P.n[j], P.H);
+    h[j] = generator(P.M.transpose(), P.LAM[j], P.n[j], P.G);
+  }
+  // biorthogonality check (Lemma 1 / Remark 2), exact
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      i128 a = 0, b = 0;
+      for (int c = 0; c < d; ++c) {
+        a += (i128)P.LAM[i][c] * g[j][c];
+        b += (i128)P.MU[i][c] * h[j][c];
+      }
+      const i64 want = (i == j) ? 1 : 0;
+      if (posmod(i64(a % P.n[i]), P.n[i]) != want || posmod(i64(b % P.n[i]), P.n[i]) != want)
+        return PFFT_ERR_OVERFLOW;
+    }
+  const int nD = P.nD, LB = P.LB;
+  // column permutation PI for the column pass (see fft_plan.hpp)
+  std::vector<int> PI(nD), PIinv(nD);
+  std::vector<int> alpha(3, 0);
+  {
+    i64 beta = posmod(P.MU[D - 1][d - 1], nD);
+    for (int j = 0; j + 1 < D; ++j) alpha[j] = int(posmod(P.MU[j][d - 1], P.n[j]));
+    const i64 gg = beta == 0 ? nD : gcd64(beta, nD);
+    const i64 span = nD / gg;
+    const i64 inv = span > 1 ? modinv(beta / gg, span) : 0;
+    for (i64 mu = 0; mu < nD; ++mu) {
+      const i64 pos = (mu % gg) * span + ((mu / gg) * inv) % span;
+      PI[mu] = int(pos);
+      PIinv[pos] = int(mu);
+    }
+  }
+  // index tables
+  std::vector<int> tab(size_t(2 * LB + 2 * nD) * d + 2 * nD);
+  int* Atab = tab.data();
+  int* Btab = Atab + size_t(LB) * d;
+  int* Ctab = Btab + size_t(nD) * d;
+  int* Etab = Ctab + size_t(LB) * d;
+  int* PIi = Etab + size_t(nD) * d;
+  int* PIf = PIi + nD;
+  std::vector<std::vector<i64>> glo(g.begin(), g.end() - 1), hlo(h.begin(), h.end() - 1);
+  std::vector<i64> coef(std::max(D - 1, 0));
+  for (int r = 0; r < LB; ++r) {
+    int x = r;
+    for (int j = D - 2; j >= 0; --j) {
+      coef[j] = x % P.n[j];
+      x /= P.n[j];
+    }
+    auto a = combo(glo, coef, P.H);
+    auto c = combo(hlo, coef, P.G);
+    for (int k = 0; k < d; ++k) {
+      Atab[size_t(r) * d + k] = int(a[k]);
+      Ctab[size_t(r) * d + k] = int(c[k]);
+    }
+  }
+  for (int e = 0; e < nD; ++e) {
+    auto b = combo({g[D - 1]}, {e}, P.H);
+    auto c = combo({h[D - 1]}, {PIinv[e]}, P.G);
+    for (int k = 0; k < d; ++k) {
+      Btab[size_t(e) * d + k] = int(b[k]);
+      Etab[size_t(e) * d + k] = int(c[k]);
+    }
+    PIi[e] = PIinv[e];
+    PIf[e] = PI[e];
+  }
+  if (int e_ = device_alloc((void**)&P.dtab, tab.size() * sizeof(int))) return pfft_status(e_);
+  if (cudaMemcpy(P.dtab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return PFFT_ERR_CUDA;
+  const size_t eb = elem_bytes(P.dtype);
+  if (int e_ = device_alloc((void**)&P.tw, size_t(nD) * eb)) return pfft_status(e_);
+  if (launch_twiddles(P.tw, nD, P.dtype, 0) != 0) return PFFT_ERR_CUDA;
+  if (D >= 2)
+    if (int e_ = device_alloc(&P.ws, size_t(P.m) * P.batch * eb)) return pfft_status(e_);
+  if (cudaDeviceSynchronize() != cudaSuccess) return PFFT_ERR_CUDA;
+
+  // pass descriptors (data pointers and modes are filled per call)
+  const int budget = P.dtype == PFFT_C64 ? 8192 : 4096;
+  for (PassArgs* p : {&P.rowp, &P.colp}) {
+    std::memset(p, 0, sizeof(PassArgs));
+    p->Atab = Atab - tab.data() + P.dtab;
+    p->Btab = Btab - tab.data() + P.dtab;
+    p->Ctab = Ctab - tab.data() + P.dtab;
+    p->Etab = Etab - tab.data() + P.dtab;
+    p->PIinv = PIi - tab.data() + P.dtab;
+    p->tw = P.tw;
+    set_box(p->boxH, P.H);
+    set_box(p->boxG, P.G);
+    p->nsub = D - 1;
+    for (int s = 0; s + 1 < D; ++s) {
+      p->sub_n[s] = P.n[s];
+      p->sub_div[s].init(uint32_t(P.n[s]));
+      p->alpha[s] = alpha[s];
+    }
+  }
+  pfft_status st = choose_and_configure(P.rowp, P, false, 64, std::max(budget, nD));
+  if (st != PFFT_OK) return st;
+  if (D >= 2) {
+    st = choose_and_configure(P.colp, P, true, 16, std::max(budget, LB));
+    if (st != PFFT_OK) return st;
+  }
+  return PFFT_OK;
+}
+
+static void release(pfft_plan_s* P) {
+  if (!P) return;
+  if (P->dtab) cudaFree(P->dtab);
+  if (P->tw) cudaFree(P->tw);
+  if (P->ws) cudaFree(P->ws);
+  delete P;
+}
+
+extern "C" pfft_status pfft_plan_create(pfft_plan* out, int d, const int64_t* M, int64_t batch,
+                                        int dtype, unsigned flags) {
+  if (!out || !M || batch < 1 || batch > 65535 || (dtype != PFFT_C64 && dtype != PFFT_C128) ||
+      flags != 0)
+    return PFFT_ERR_ARG;
+  *out = nullptr;
+  pfft_plan_s* P = new (std::nothrow) pfft_plan_s;
+  if (!P) return PFFT_ERR_OOM;
+  P->batch = batch;
+  P->dtype = dtype;
+  pfft_status st;
+  try {
+    st = plan_host(*P, d, M);
+    if (st == PFFT_OK && P->m * batch >= (int64_t(1) << 40)) st = PFFT_ERR_OVERFLOW;
+    if (st == PFFT_OK) st = plan_device(*P);
+  } catch (const LatticeError& e) {
+    st = pfft_status(e.code);
+  }
+  if (st != PFFT_OK) {
+    release(P);
+    return st;
+  }
+  *out = P;
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pfft_plan_destroy(pfft_plan p) {
+  if (!p) return PFFT_ERR_ARG;
+  release(p);
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pfft_plan_info(pfft_plan p, int64_t* m, int* dM, int64_t* eps, int64_t* in_box,
+                                      int64_t* out_box) {
+  if (!p) return PFFT_ERR_ARG;
+  if (m) *m = p->m;
+  if (dM) *dM = p->D;
+  for (int i = 0; i < p->d; ++i) {
+    if (eps) eps[i] = p->eps[i];
+    if (in_box) in_box[i] = p->H(i, i);
+    if (out_box) out_box[i] = p->G(i, i);
+  }
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pfft_index_map(pfft_plan p, int which, int64_t* coords) {
+  if (!p || !coords) return PFFT_ERR_ARG;
+  const int d = p->d;
+  std::vector<i64> v(d);
+  for (i64 s = 0; s < p->m; ++s) {
+    switch (which) {
+      case PFFT_MAP_INPUT_BOX:
+        box_point(p->H, s, coords + s * d);
+        break;
+      case PFFT_MAP_OUTPUT_BOX:
+        box_point(p->G, s, coords + s * d);
+        break;
+      case PFFT_MAP_INPUT_SNF:
+      case PFFT_MAP_OUTPUT_SNF: {
+        const bool in = which == PFFT_MAP_INPUT_SNF;
+        box_point(in ? p->H : p->G, s, v.data());
+        for (int j = 0; j < p->D; ++j) {
+          i128 acc = 0;
+          for (int c = 0; c < d; ++c) acc += (i128)(in ? p->LAM[j][c] : p->MU[j][c]) * v[c];
+          coords[s * p->D + j] = posmod(i64(acc % p->n[j]), p->n[j]);
+        }
+        break;
+      }
+      default:
+        return PFFT_ERR_ARG;
+    }
+  }
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pfft_device_index_map(pfft_plan p, int which, int64_t* slots, void* stream) {
+  if (!p || !slots || (which != PFFT_MAP_INPUT_BOX && which != PFFT_MAP_OUTPUT_BOX)) return PFFT_ERR_ARG;
+  if (p->D == 0) {
+    int64_t zero = 0;
+    return cudaMemcpyAsync(slots, &zero, sizeof(zero), cudaMemcpyHostToDevice, (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? PFFT_OK
+               : PFFT_ERR_CUDA;
+  }
+  PassArgs a = p->rowp;
+  return launch_index_probe(a, a, which == PFFT_MAP_INPUT_BOX ? 0 : 1, slots, (cudaStream_t)stream) == 0
+             ? PFFT_OK
+             : PFFT_ERR_CUDA;
+}
+
+static pfft_status run_pass(pfft_plan_s* P, PassArgs a, int load, int store, int cin, int cout,
+                            double scale, const void* in, void* out, cudaStream_t s, int which) {
+  a.load_mode = load;
+  a.store_mode = store;
+  a.conj_in = cin;
+  a.conj_out = cout;
+  a.scale = scale;
+  a.in = in;
+  a.out = out;
+  P->prof.begin(which, s);
+  if (launch_pass(a, P->dtype, s) != 0) return PFFT_ERR_CUDA;
+  P->prof.end(which, s);
+  return PFFT_OK;
+}
+
+static pfft_status transform(pfft_plan p, const void* in, void* out, void* stream, bool inverse) {
+  if (!p || !in || !out || in == out) return PFFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double scale = 1.0 / std::sqrt(double(p->m));
+  if (p->D == 0) {
+    const size_t bytes = size_t(p->batch) * elem_bytes(p->dtype);
+    return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? PFFT_OK
+                                                                                       : PFFT_ERR_CUDA;
+  }
+  const int ci = inverse ? 1 : 0;
+  if (p->D == 1) {
+    return run_pass(p, p->rowp, inverse ? MAP_BOX_G : MAP_BOX_H, inverse ? MAP_BOX_H : MAP_BOX_G, ci, ci,
+                    scale, in, out, s, 0);
+  }
+  if (!inverse) {
+    pfft_status st = run_pass(p, p->rowp, MAP_BOX_H, MAP_WS, 0, 0, 1.0, in, p->ws, s, 0);
+    if (st != PFFT_OK) return st;
+    return run_pass(p, p->colp, MAP_WS, MAP_BOX_G, 0, 0, scale, p->ws, out, s, 1);
+  }
+  pfft_status st = run_pass(p, p->colp, MAP_BOX_G, MAP_WS, 1, 0, 1.0, in, p->ws, s, 1);
+  if (st != PFFT_OK) return st;
+  return run_pass(p, p->rowp, MAP_WS, MAP_BOX_H, 0, 1, scale, p->ws, out, s, 0);
+}
+
+extern "C" pfft_status pfft_forward(pfft_plan p, const void* in, void* out, void* stream) {
+  return transform(p, in, out, stream, false);
+}
+
+extern "C" pfft_status pfft_inverse(pfft_plan p, const void* in, void* out, void* stream) {
+  return transform(p, in, out, stream, true);
+}
+
+static const char* kPassNames[] = {"row_pass", "col_pass"};
+
+extern "C" pfft_status pfft_profile_enable(pfft_plan p, int enable) {
+  if (!p) return PFFT_ERR_ARG;
+  return p->prof.enable(enable != 0, 2, kPassNames) ? PFFT_OK : PFFT_ERR_CUDA;
+}
+
+extern "C" pfft_status pfft_profile_read(pfft_plan p, const char** names, int64_t* launches, double* ms,
+                                         int cap, int* n) {
+  if (!p) return PFFT_ERR_ARG;
+  return p->prof.read(names, launches, ms, cap, n) ? PFFT_OK : PFFT_ERR_CUDA;
+}

@@ -1,0 +1,90 @@
+// Plan structures shared by the host planner and the transform kernels.
+//
+// The transform runs in Smith coordinates (Theorem 1): with the non-trivial
+// elementary divisors n_1 | ... | n_D (D = d_M <= 3), the data is viewed as a
+// logical LB x nD array, nD = n_D the longest cycle and LB = n_1 ... n_{D-1}
+// the product of the others (eq. (KroneckerFFT): "blockwise" transforms of
+// length n_D, then the transforms over the remaining cycles on interleaved
+// data).  Two kernels implement the two halves:
+//
+//   row pass    one CTA holds T full rows (length nD) in shared memory and
+//               runs the length-nD DFT; the gather from the input box (or the
+//               scatter to it, inverse direction) is fused into its load
+//               (store).
+//   column pass one CTA holds all LB rows of T columns and runs the
+//               (D-1)-dimensional DFT over the other cycles; the scatter to
+//               the output box (gather from it, inverse) is fused into its
+//               store (load).
+//
+// Between them the data sits in a workspace laid out [LB][nD] whose columns
+// are permuted (PI) so that the columns one column-pass CTA needs are
+// adjacent, and the same CTA's output-box writes come in contiguous runs.
+#pragma once
+#include <stdint.h>
+
+#include "device_common.cuh"
+
+namespace pfft {
+
+enum MapMode { MAP_WS = 0, MAP_BOX_H = 1, MAP_BOX_G = 2 };
+
+constexpr int kMaxStages = 16;
+constexpr int kMaxSub = 3;
+constexpr int kMaxThreads = 512;
+constexpr int kRadixOrder[14] = {16, 8, 4, 2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
+
+// One radix stage of a Stockham autosort DFT along one axis of a pencil.
+struct StageDesc {
+  int R;       // radix
+  int a;       // length of the axis
+  int aR;      // a / R
+  int sigma;   // stride of the axis inside the pencil (elements)
+  int Ns;      // product of the radices of the earlier stages on this axis
+  int twstep;  // nD / (Ns * R): index step into the omega_{nD} table
+  FastDiv div_aR, div_sigma, div_Ns;
+};
+
+struct PassArgs {
+  // geometry
+  int L;        // pencil length (row pass: nD; column pass: LB)
+  int T;        // pencils per CTA
+  int nD, LB, m, d;
+  int cols;     // 1: column pass, 0: row pass
+  int nstages;
+  int cnt[14];  // stages per radix, in the order of kRadixOrder
+  int pow2;     // all radices are powers of two
+  StageDesc st[kMaxStages];
+  FastDiv divT, divnD;
+  int nthreads;
+  int smem_bytes;
+  int groups;   // CTAs per signal
+  int batch;
+  // data
+  int load_mode, store_mode;
+  int conj_in, conj_out;
+  double scale;
+  const void* in;
+  void* out;
+  // tables (device, d int32 per entry)
+  const int* Atab;   // [LB]  box(H) point of sum_{j<D} lambda_j g_j
+  const int* Btab;   // [nD]  box(H) point of lambda_D g_D
+  const int* Ctab;   // [LB]  box(G) point of sum_{j<D} mu_j h_j
+  const int* Etab;   // [nD]  box(G) point of PIinv[pos] h_D   (indexed by position)
+  const int* PIinv;  // [nD]  column position -> mu_D (or lambda_D)
+  const void* tw;    // [nD]  omega_{nD}^t = exp(-2 pi i t / nD)
+  BoxDesc boxH, boxG;
+  // shear of the column pass: a run of consecutive output slots along the
+  // fastest output coordinate visits (mu_<D + t alpha, position + t).
+  int nsub;
+  int sub_n[kMaxSub];
+  FastDiv sub_div[kMaxSub];
+  int alpha[kMaxSub];
+};
+
+// Host-side launcher (fft_kernels.cu).
+int launch_pass(const PassArgs& a, int dtype, cudaStream_t s);
+int launch_twiddles(void* tw, int nD, int dtype, cudaStream_t s);
+int launch_index_probe(const PassArgs& rowp, const PassArgs& colp, int which, int64_t* out,
+                       cudaStream_t s);
+
+}  // namespace pfft

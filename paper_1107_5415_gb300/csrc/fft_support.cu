@@ -1,0 +1,61 @@
+// Transform support kernels: pass dispatch, twiddle table, index probe.
+#include <cuda_runtime.h>
+
+#include "fft_plan.hpp"
+
+namespace pfft {
+
+int launch_pass_pow2(const PassArgs& a, int dtype, cudaStream_t s);
+int launch_pass_generic(const PassArgs& a, int dtype, cudaStream_t s);
+
+int launch_pass(const PassArgs& a, int dtype, cudaStream_t s) {
+  return a.pow2 ? launch_pass_pow2(a, dtype, s) : launch_pass_generic(a, dtype, s);
+}
+
+// Twiddle table omega_{nD}^t = exp(-2 pi i t / nD), t in [0, nD): exact
+// integer t, FP64 sincospi, rounded to the working precision.
+template <typename C>
+__global__ void twiddle_kernel(C* tw, int nD) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nD) return;
+  double s, c;
+  sincospi(2.0 * double(t) / double(nD), &s, &c);
+  tw[t] = cmake<C>(decltype(C::x)(c), decltype(C::x)(-s));
+}
+
+int launch_twiddles(void* tw, int nD, int dtype, cudaStream_t s) {
+  const int blk = 256, grd = (nD + blk - 1) / blk;
+  if (dtype == 0)
+    twiddle_kernel<float2><<<grd, blk, 0, s>>>(static_cast<float2*>(tw), nD);
+  else
+    twiddle_kernel<double2><<<grd, blk, 0, s>>>(static_cast<double2*>(tw), nD);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Index probe: for every Smith coordinate vector (row-major, flattened as
+// row * nD + element), the box slot the transform kernels read (input map,
+// which = 0) or write (output map, which = 1), evaluated with the same
+// device code as the passes.  For the output map the element index is the
+// Smith coordinate mu_D (converted to its workspace position).
+__global__ void index_probe_kernel(PassArgs a, const int* __restrict__ PI, int which, int64_t* out) {
+  const int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (w >= a.m) return;
+  const int row = int(w / a.nD), e = int(w - int64_t(row) * a.nD);
+  int slot;
+  if (which == 0)
+    slot = box_sum_slot(a.boxH, a.Atab + row * a.d, a.Btab + e * a.d);
+  else
+    slot = box_sum_slot(a.boxG, a.Ctab + row * a.d, a.Etab + PI[e] * a.d);
+  out[w] = slot;
+}
+
+int launch_index_probe(const PassArgs& rowp, const PassArgs& colp, int which, int64_t* out,
+                       cudaStream_t s) {
+  (void)colp;
+  const int blk = 256;
+  const int grd = int((int64_t(rowp.m) + blk - 1) / blk);
+  index_probe_kernel<<<grd, blk, 0, s>>>(rowp, rowp.PIinv + rowp.nD, which, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace pfft

@@ -1,0 +1,560 @@
+// Fast wavelet split step (Section 5.3, step 4) with the Dirichlet symbols of
+// Section 6.2, its exact inverse and its adjoint: plans (host, exact integer
+// setup) and the sm_103a kernel.
+//
+// One level, M = J N with |det J| = 2.  G(M^T) -> G(N^T) is onto with kernel
+// N^T G(J^T), so the fibre of g in G(N^T) is {h0, h1} = {g, g + N^T l1}, l1
+// the non-zero class of G(J^T).  The kernel walks the slots g of the box of
+// H(N^T) (coalesced writes); g already lies in the box of H(M^T) because the
+// diagonal of H(M^T) dominates that of H(N^T) (M^T Z^d is a sublattice of
+// N^T Z^d), and h1 is g plus a fixed box point, reduced with at most one
+// column step per coordinate.
+//
+// Scaling symbol, evaluated in the periodised form
+//     A(h) = sqrt(|det J| w(N^{-T} h)),   w(t) = sum_{n in J^T Z^d} prod_j B(t_j + n_j),
+// with B the indicator of [-1/2, 1/2] taking 1/2 on the boundary (Dirichlet,
+// equal to the case formula of Section 6.2), or, for the de la Vallee Poussin
+// reading, A(h) = sqrt|det J| w(N^{-T} h) with B(s) = clamp(((1+eta)/2-|s|)/eta, 0, 1).
+// N^{-T} h = J^T M^{-T} h is formed from the exact integer numerators
+// adj(M^T) h over |det M|.  Wavelet symbol B(h) = A(h + N^T l1)
+// exp(-2 pi i h^T N^{-1} z), with h^T N^{-1} z = h^T M^{-1} (J z) read from a
+// two-level table of exp(-2 pi i t / |det M|) built in FP64.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pfft.h"
+#include "device_common.cuh"
+#include "lattice.hpp"
+#include "plan_common.hpp"
+
+namespace pfft {
+
+constexpr int kLoBits = 11;
+
+struct LevelDesc {
+  int d;
+  int mN;                // points of G(N^T)
+  int mM;                // points of G(M^T)
+  BoxDesc HM;            // box of H(M^T)
+  int HNext[4];          // extents of the box of H(N^T)
+  FastDiv divHN[4];
+  int shift1[4];         // box(H(M^T)) point of N^T l1
+  long long adjMT[16];   // adj(M^T)
+  long long q;           // |det M|
+  int sM;                // sign det M
+  int J[16];
+  long long adjJT[16];
+  int aJ;                // |det J|
+  long long phw[4];      // adj(M) (J z): phase numerator of h is sM * h . phw mod q
+  int symbol;
+  double eta;
+  const void* tab_lo;    // exp(-2 pi i t / q), t < 2^kLoBits
+  const void* tab_hi;    // exp(-2 pi i (t << kLoBits) / q)
+};
+
+__device__ __forceinline__ long long floordiv_ll(long long a, long long b) {  // b > 0
+  long long q = a / b;
+  if ((a % b) != 0 && a < 0) --q;
+  return q;
+}
+
+template <typename Rl>
+__device__ Rl scaling_symbol(const LevelDesc& L, const int* h) {
+  const int d = L.d;
+  const long long q = L.q;
+  long long v[4], u[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (j >= d) break;
+    long long p = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i < d) p += L.adjMT[j * d + i] * (long long)h[i];
+    p *= L.sM;
+    u[j] = p - q * floordiv_ll(2 * p + q, 2 * q);  // centred numerator, M^{-T} h mod 1
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (j >= d) break;
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i < d) s += (long long)L.J[i * d + j] * u[i];
+    v[j] = s;  // N^{-T} h = v / q
+  }
+  // candidate integer shifts per coordinate with their weights
+  int ncand[4];
+  long long nval[4][3];
+  Rl wts[4][3];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    ncand[j] = 1;
+    if (j >= d) continue;
+    const long long r = floordiv_ll(2 * v[j] + q, 2 * q);
+    const long long c = v[j] - q * r;  // in [-q/2, q/2)
+    ncand[j] = 0;
+    if (L.symbol == PWT_DIRICHLET) {
+      if (2 * c == -q) {
+        nval[j][0] = -r;
+        wts[j][0] = Rl(0.5);
+        nval[j][1] = -r + 1;
+        wts[j][1] = Rl(0.5);
+        ncand[j] = 2;
+      } else {
+        nval[j][0] = -r;
+        wts[j][0] = Rl(1);
+        ncand[j] = 1;
+      }
+    } else {
+      const Rl eta = Rl(L.eta);
+#pragma unroll
+      for (int o = -1; o <= 1; ++o) {
+        const Rl s = Rl(c + (long long)o * q) / Rl(q);
+        Rl b = (Rl(0.5) * (Rl(1) + eta) - (s < 0 ? -s : s)) / eta;
+        if (b > Rl(0)) {
+          nval[j][ncand[j]] = -r + o;
+          wts[j][ncand[j]] = b < Rl(1) ? b : Rl(1);
+          ++ncand[j];
+        }
+      }
+      if (ncand[j] == 0) return Rl(0);
+    }
+  }
+  Rl w = 0;
+  int idx[4] = {0, 0, 0, 0};
+  for (;;) {
+    bool member = true;  // n in J^T Z^d  <=>  adj(J^T) n = 0 mod |det J|
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i >= d) break;
+      long long s = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < d) s += L.adjJT[i * d + j] * nval[j][idx[j]];
+      if (s % L.aJ != 0) member = false;
+    }
+    if (member) {
+      Rl p = 1;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < d) p *= wts[j][idx[j]];
+      w += p;
+    }
+    int j = d - 1;
+    while (j >= 0 && ++idx[j] == ncand[j]) idx[j--] = 0;
+    if (j < 0) break;
+  }
+  if (L.symbol == PWT_DIRICHLET) return sqrt(Rl(L.aJ) * w);
+  return sqrt(Rl(L.aJ)) * w;
+}
+
+template <typename C>
+__device__ __forceinline__ C wavelet_phase(const LevelDesc& L, const int* h) {
+  long long t = 0;  // each product < 2^62; reduce term by term
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (i < L.d) t += ((long long)h[i] * L.phw[i]) % L.q;
+  t = (L.sM * t) % L.q;
+  if (t < 0) t += L.q;
+  const C* lo = static_cast<const C*>(L.tab_lo);
+  const C* hi = static_cast<const C*>(L.tab_hi);
+  return cmul(hi[t >> kLoBits], lo[t & ((1 << kLoBits) - 1)]);
+}
+
+// mode 0: decompose c -> (d1, d2); 1: reconstruct; 2: adjoint.
+template <typename C, int MODE>
+__global__ void __launch_bounds__(256) split_kernel(LevelDesc L, int batch, const C* __restrict__ cin,
+                                                    C* __restrict__ cout, const C* __restrict__ d1in,
+                                                    const C* __restrict__ d2in, C* __restrict__ d1out,
+                                                    C* __restrict__ d2out) {
+  using Rl = decltype(C::x);
+  const long long total = (long long)L.mN * batch;
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
+       w += (long long)gridDim.x * blockDim.x) {
+    const int b = int(w / L.mN);
+    const int gs = int(w - (long long)b * L.mN);
+    int g[4] = {0, 0, 0, 0}, h1[4] = {0, 0, 0, 0};
+    int s = gs;
+    for (int r = L.d - 1; r >= 0; --r) {
+      const int qd = L.divHN[r].div(s);
+      g[r] = s - qd * L.HNext[r];
+      s = qd;
+    }
+    int slot0 = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (r < L.d) {
+        h1[r] = g[r] + L.shift1[r];
+        slot0 += g[r] * L.HM.stride[r];
+      }
+    }
+    box_fix(L.HM, h1);
+    int slot1 = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (r < L.d) slot1 += h1[r] * L.HM.stride[r];
+    const Rl A0 = scaling_symbol<Rl>(L, g), A1 = scaling_symbol<Rl>(L, h1);
+    const C e0 = wavelet_phase<C>(L, g), e1 = wavelet_phase<C>(L, h1);
+    const C B0 = cscale(e0, A1), B1 = cscale(e1, A0);
+    const Rl r2 = Rl(0.70710678118654752440);
+    const long long oM = (long long)b * L.mM, oN = (long long)b * L.mN;
+    if (MODE == 0) {
+      const C c0 = cin[oM + slot0], c1 = cin[oM + slot1];
+      d1out[oN + gs] = cscale(cadd(cscale(c0, A0), cscale(c1, A1)), r2);
+      d2out[oN + gs] = cscale(cadd(cmul(cconj(B0), c0), cmul(cconj(B1), c1)), r2);
+    } else {
+      const C a = d1in[oN + gs], bb = d2in[oN + gs];
+      const Rl S = A0 * A0 + A1 * A1;
+      const Rl fac = (MODE == 1) ? Rl(1.41421356237309504880) / S : r2;
+      cout[oM + slot0] = cscale(cadd(cscale(a, A0), cmul(B0, bb)), fac);
+      cout[oM + slot1] = cscale(cadd(cscale(a, A1), cmul(B1, bb)), fac);
+    }
+  }
+}
+
+template <typename C>
+__global__ void phase_table_kernel(C* lo, C* hi, long long q, int nhi) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  using Rl = decltype(C::x);
+  double s, c;
+  if (t < (1 << kLoBits)) {
+    sincospi(2.0 * double(t % q) / double(q), &s, &c);
+    lo[t] = cmake<C>(Rl(c), Rl(-s));
+  }
+  if (t < nhi) {
+    const long long a = ((long long)t << kLoBits) % q;
+    sincospi(2.0 * double(a) / double(q), &s, &c);
+    hi[t] = cmake<C>(Rl(c), Rl(-s));
+  }
+}
+
+template <typename C>
+static int launch_split(const LevelDesc& L, int batch, int mode, const void* cin, void* cout,
+                        const void* d1in, const void* d2in, void* d1out, void* d2out, cudaStream_t s) {
+  const long long total = (long long)L.mN * batch;
+  const int blk = 256;
+  long long grd = (total + blk - 1) / blk;
+  if (grd > 152 * 64) grd = 152 * 64;
+  auto c = [](const void* p) { return static_cast<const C*>(p); };
+  auto m = [](void* p) { return static_cast<C*>(p); };
+  if (mode == 0)
+    split_kernel<C, 0><<<int(grd), blk, 0, s>>>(L, batch, c(cin), nullptr, nullptr, nullptr, m(d1out),
+                                                 m(d2out));
+  else if (mode == 1)
+    split_kernel<C, 1><<<int(grd), blk, 0, s>>>(L, batch, nullptr, m(cout), c(d1in), c(d2in), nullptr,
+                                                 nullptr);
+  else
+    split_kernel<C, 2><<<int(grd), blk, 0, s>>>(L, batch, nullptr, m(cout), c(d1in), c(d2in), nullptr,
+                                                 nullptr);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace pfft
+
+using namespace pfft;
+
+struct pwt_plan_s {
+  int d = 0, levels = 0, symbol = 0, dtype = 0;
+  int64_t batch = 0;
+  double eta = 0;
+  std::vector<IMat> Ms;       // M_1 .. M_{levels+1} (M_{l+1} = N_l)
+  std::vector<i64> sizes;     // |det M_l|
+  std::vector<IMat> boxes;    // H(M_l^T)
+  std::vector<LevelDesc> lv;  // device descriptors
+  void* tables = nullptr;     // phase tables of all levels
+  void* ws[2] = {nullptr, nullptr};
+  Profiler prof;
+};
+
+static size_t cbytes(int dtype) { return dtype == PFFT_C64 ? 8 : 16; }
+
+static void release(pwt_plan_s* P) {
+  if (!P) return;
+  if (P->tables) cudaFree(P->tables);
+  for (auto p : P->ws)
+    if (p) cudaFree(p);
+  delete P;
+}
+
+// The non-zero class of G(J^T) = Z^d / J^T Z^d: a unit vector outside J^T Z^d.
+static bool nonzero_class(const IMat& J, std::vector<i64>& l1) {
+  const int d = J.d;
+  IMat A = adjugate(J.transpose());
+  const i64 D = determinant(J);
+  const i64 aD = D < 0 ? -D : D;
+  for (int i = 0; i < d; ++i) {
+    // e_i in J^T Z^d  <=>  adj(J^T) e_i = 0 mod |det J|
+    bool inside = true;
+    for (int r = 0; r < d; ++r)
+      if (posmod(A(r, i), aD) != 0) inside = false;
+    if (!inside) {
+      l1.assign(d, 0);
+      l1[i] = 1;
+      return true;
+    }
+  }
+  return false;
+}
+
+// u = J z for the non-zero z of P(J) = Lambda(J) cap [-1/2, 1/2)^d.
+static bool wavelet_shift(const IMat& J, std::vector<i64>& u) {
+  const int d = J.d;
+  const i64 D = determinant(J);
+  const i64 aD = D < 0 ? -D : D;
+  const int sD = D < 0 ? -1 : 1;
+  IMat A = adjugate(J);
+  IMat H = hermite_normal_form(J);
+  // enumerate the box of H(J) (the classes of G(J)); z = J^{-1} y, centred
+  std::vector<i64> y(d, 0);
+  for (i64 s = 0; s < aD; ++s) {
+    box_point(H, s, y.data());
+    std::vector<i64> num(d);  // z = num / aD
+    bool zero = true;
+    for (int i = 0; i < d; ++i) {
+      i128 t = 0;
+      for (int k = 0; k < d; ++k) t += (i128)A(i, k) * y[k];
+      t *= sD;
+      // centre into [-1/2, 1/2): num - aD * floor((2 num + aD) / (2 aD))
+      i64 v = i64(t);
+      v -= aD * floordiv(2 * v + aD, 2 * aD);
+      num[i] = v;
+      if (v != 0) zero = false;
+    }
+    if (zero) continue;
+    u.assign(d, 0);
+    for (int i = 0; i < d; ++i) {
+      i128 t = 0;
+      for (int k = 0; k < d; ++k) t += (i128)J(i, k) * num[k];
+      if (t % aD != 0) return false;
+      u[i] = i64(t / aD);
+    }
+    return true;
+  }
+  return false;
+}
+
+static pfft_status plan_levels(pwt_plan_s& P, const int64_t* Mv, const int64_t* Jv) {
+  const int d = P.d;
+  IMat M(d);
+  for (int i = 0; i < d * d; ++i) {
+    if (Mv[i] >= (int64_t(1) << 24) || Mv[i] <= -(int64_t(1) << 24)) return PFFT_ERR_OVERFLOW;
+    M.a[i] = Mv[i];
+  }
+  i64 det = determinant(M);
+  if (det == 0) return PFFT_ERR_SINGULAR;
+  if ((det < 0 ? -det : det) >= (i64(1) << 31)) return PFFT_ERR_OVERFLOW;
+  P.Ms.push_back(M);
+  for (int l = 0; l < P.levels; ++l) {
+    IMat J(d);
+    for (int i = 0; i < d * d; ++i) J.a[i] = Jv[size_t(l) * d * d + i];
+    const i64 dJ = determinant(J);
+    if (dJ == 0) return PFFT_ERR_SINGULAR;
+    if (dJ != 2 && dJ != -2) return PFFT_ERR_UNSUPPORTED;
+    const IMat& Mc = P.Ms.back();
+    // N = J^{-1} M = adj(J) M / det J, must be integral
+    IMat N = matmul(adjugate(J), Mc);
+    for (auto& x : N.a) {
+      if (x % dJ != 0) return PFFT_ERR_NOT_INTEGRAL;
+      x /= dJ;
+    }
+    const i64 detM = determinant(Mc);
+    const i64 q = detM < 0 ? -detM : detM;
+    LevelDesc L;
+    std::memset(&L, 0, sizeof(L));
+    L.d = d;
+    IMat HM = hermite_normal_form(Mc.transpose());
+    IMat HN = hermite_normal_form(N.transpose());
+    L.mM = int(q);
+    L.mN = int(q / 2);
+    L.HM.d = d;
+    int stride = 1;
+    for (int r = d - 1; r >= 0; --r) {
+      for (int c = 0; c < d; ++c) L.HM.H[r][c] = int(HM(r, c));
+      L.HM.stride[r] = stride;
+      stride *= int(HM(r, r));
+      L.HNext[r] = int(HN(r, r));
+      L.divHN[r].init(uint32_t(HN(r, r)));
+      if (HN(r, r) > HM(r, r)) return PFFT_ERR_OVERFLOW;  // cannot happen for M = J N
+    }
+    std::vector<i64> l1, u;
+    if (!nonzero_class(J, l1) || !wavelet_shift(J, u)) return PFFT_ERR_UNSUPPORTED;
+    std::vector<i64> sh(d, 0);
+    for (int i = 0; i < d; ++i)
+      for (int k = 0; k < d; ++k) sh[i] += N(k, i) * l1[k];  // N^T l1
+    box_reduce(HM, sh.data());
+    for (int i = 0; i < d; ++i) L.shift1[i] = int(sh[i]);
+    IMat adjMT = adjugate(Mc.transpose());
+    IMat adjM = adjugate(Mc);
+    IMat adjJT = adjugate(J.transpose());
+    for (int i = 0; i < d * d; ++i) {
+      L.adjMT[i] = adjMT.a[i];
+      L.J[i] = int(J.a[i]);
+      L.adjJT[i] = adjJT.a[i];
+    }
+    L.q = q;
+    L.sM = detM < 0 ? -1 : 1;
+    L.aJ = 2;
+    for (int i = 0; i < d; ++i) {
+      i128 t = 0;
+      for (int k = 0; k < d; ++k) t += (i128)adjM(i, k) * u[k];
+      t %= q;  // only needed mod q
+      L.phw[i] = (long long)t;
+    }
+    // overflow guards for the device's int64 arithmetic: |adj(M^T)_ij| h_j summed
+    // over d terms must stay below 2^62 for every box point h
+    for (int i = 0; i < d; ++i) {
+      i128 bound = 0;
+      for (int k = 0; k < d; ++k) {
+        const i64 a = adjMT(i, k) < 0 ? -adjMT(i, k) : adjMT(i, k);
+        bound += (i128)a * HM(k, k);
+      }
+      if (bound >= ((i128)1 << 60)) return PFFT_ERR_OVERFLOW;
+    }
+    L.symbol = P.symbol;
+    L.eta = P.eta;
+    P.lv.push_back(L);
+    P.boxes.push_back(HM);
+    P.sizes.push_back(q);
+    P.Ms.push_back(N);
+  }
+  {
+    IMat HL = hermite_normal_form(P.Ms.back().transpose());
+    P.boxes.push_back(HL);
+    const i64 dl = determinant(P.Ms.back());
+    P.sizes.push_back(dl < 0 ? -dl : dl);
+  }
+  return PFFT_OK;
+}
+
+static pfft_status plan_device(pwt_plan_s& P) {
+  const size_t cb = cbytes(P.dtype);
+  size_t total = 0;
+  std::vector<size_t> offs;
+  for (auto& L : P.lv) {
+    const int nhi = int((L.q + (1LL << kLoBits) - 1) >> kLoBits);
+    offs.push_back(total);
+    total += size_t((1 << kLoBits) + nhi) * cb;
+  }
+  if (int e_ = device_alloc((void**)&P.tables, total)) return pfft_status(e_);
+  for (size_t l = 0; l < P.lv.size(); ++l) {
+    LevelDesc& L = P.lv[l];
+    const int nhi = int((L.q + (1LL << kLoBits) - 1) >> kLoBits);
+    char* base = static_cast<char*>(P.tables) + offs[l];
+    L.tab_lo = base;
+    L.tab_hi = base + size_t(1 << kLoBits) * cb;
+    const int n = std::max(1 << kLoBits, nhi);
+    const int blk = 256, grd = (n + blk - 1) / blk;
+    if (P.dtype == PFFT_C64)
+      phase_table_kernel<float2><<<grd, blk>>>((float2*)L.tab_lo, (float2*)L.tab_hi, L.q, nhi);
+    else
+      phase_table_kernel<double2><<<grd, blk>>>((double2*)L.tab_lo, (double2*)L.tab_hi, L.q, nhi);
+    if (cudaGetLastError() != cudaSuccess) return PFFT_ERR_CUDA;
+  }
+  if (P.levels > 1) {
+    const size_t half = size_t(P.sizes[0] / 2) * P.batch * cb;
+    for (int i = 0; i < 2; ++i)
+      if (int e_ = device_alloc((void**)&P.ws[i], half)) return pfft_status(e_);
+  }
+  return cudaDeviceSynchronize() == cudaSuccess ? PFFT_OK : PFFT_ERR_CUDA;
+}
+
+extern "C" pfft_status pwt_plan_create(pwt_plan* out, int d, const int64_t* M, int levels,
+                                       const int64_t* J, int symbol, double eta, int64_t batch,
+                                       int dtype, unsigned flags) {
+  if (!out || !M || !J || d < 1 || d > 4 || levels < 1 || levels > 64 || batch < 1 ||
+      batch > (int64_t(1) << 20) || (dtype != PFFT_C64 && dtype != PFFT_C128) || flags != 0 ||
+      (symbol != PWT_DIRICHLET && symbol != PWT_DLVP) ||
+      (symbol == PWT_DLVP && !(eta > 0.0 && eta < 1.0)))
+    return PFFT_ERR_ARG;
+  *out = nullptr;
+  pwt_plan_s* P = new (std::nothrow) pwt_plan_s;
+  if (!P) return PFFT_ERR_OOM;
+  P->d = d;
+  P->levels = levels;
+  P->symbol = symbol;
+  P->eta = eta;
+  P->batch = batch;
+  P->dtype = dtype;
+  pfft_status st;
+  try {
+    st = plan_levels(*P, M, J);
+    if (st == PFFT_OK && P->sizes[0] * batch >= (int64_t(1) << 40)) st = PFFT_ERR_OVERFLOW;
+    if (st == PFFT_OK) st = plan_device(*P);
+  } catch (const LatticeError& e) {
+    st = pfft_status(e.code);
+  }
+  if (st != PFFT_OK) {
+    release(P);
+    return st;
+  }
+  *out = P;
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pwt_plan_destroy(pwt_plan p) {
+  if (!p) return PFFT_ERR_ARG;
+  release(p);
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pwt_plan_info(pwt_plan p, int level, int64_t* n, int64_t* box) {
+  if (!p || level < 0 || level > p->levels) return PFFT_ERR_ARG;
+  if (n) *n = p->sizes[level];
+  if (box)
+    for (int i = 0; i < p->d; ++i) box[i] = p->boxes[level](i, i);
+  return PFFT_OK;
+}
+
+static int run_level(pwt_plan_s* P, int l, int mode, const void* cin, void* cout, const void* d1in,
+                     const void* d2in, void* d1out, void* d2out, cudaStream_t s) {
+  P->prof.begin(0, s);
+  int rc = P->dtype == PFFT_C64
+               ? launch_split<float2>(P->lv[l], int(P->batch), mode, cin, cout, d1in, d2in, d1out, d2out, s)
+               : launch_split<double2>(P->lv[l], int(P->batch), mode, cin, cout, d1in, d2in, d1out, d2out, s);
+  P->prof.end(0, s);
+  return rc;
+}
+
+extern "C" pfft_status pwt_decompose(pwt_plan p, const void* c_hat, void* scaling, void* const* wavelets,
+                                     void* stream) {
+  if (!p || !c_hat || !scaling || !wavelets) return PFFT_ERR_ARG;
+  for (int l = 0; l < p->levels; ++l)
+    if (!wavelets[l]) return PFFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const void* cur = c_hat;
+  for (int l = 0; l < p->levels; ++l) {
+    void* d1 = (l == p->levels - 1) ? scaling : p->ws[l & 1];
+    if (run_level(p, l, 0, cur, nullptr, nullptr, nullptr, d1, wavelets[l], s) != 0) return PFFT_ERR_CUDA;
+    cur = d1;
+  }
+  return PFFT_OK;
+}
+
+static pfft_status synthesise(pwt_plan p, const void* scaling, const void* const* wavelets, void* c_hat,
+                              void* stream, int mode) {
+  if (!p || !c_hat || !scaling || !wavelets) return PFFT_ERR_ARG;
+  for (int l = 0; l < p->levels; ++l)
+    if (!wavelets[l]) return PFFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const void* cur = scaling;
+  for (int l = p->levels - 1; l >= 0; --l) {
+    void* dst = (l == 0) ? c_hat : p->ws[l & 1];
+    if (run_level(p, l, mode, nullptr, dst, cur, wavelets[l], nullptr, nullptr, s) != 0) return PFFT_ERR_CUDA;
+    cur = dst;
+  }
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pwt_reconstruct(pwt_plan p, const void* scaling, const void* const* wavelets,
+                                       void* c_hat, void* stream) {
+  return synthesise(p, scaling, wavelets, c_hat, stream, 1);
+}
+
+extern "C" pfft_status pwt_adjoint(pwt_plan p, const void* scaling, const void* const* wavelets,
+                                   void* c_hat, void* stream) {
+  return synthesise(p, scaling, wavelets, c_hat, stream, 2);
+}

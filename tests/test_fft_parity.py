@@ -1,0 +1,182 @@
+"""GPU parity of the pattern FFT against the FP64 oracle (through the C ABI).
+
+Bar: bit-exact index maps; relative L2 error <= 1e-5 (complex64) or 1e-12
+(complex128).  Small patterns are compared on every output; the batched
+2^24-point workload in the benchmark's launch configuration is compared on
+4096 seeded random frequencies evaluated by the oracle's direct sum."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import lattice as L
+import paper_1107_5415_gb300 as pf
+import seeded_inputs as SI
+from parity_util import TOL, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+SMALL = [
+    SI.M_SMALL_2D,                          # cycles (16, 272): radix 17
+    [[4, -3], [4, 5]],                      # Example 1: one cycle of 32
+    [[6, 2], [-2, 6]],                      # (2, 20): radix 5
+    [[8, 2], [2, -4]],                      # negative determinant, (2, 18)
+    [[12]],                                 # d = 1
+    [[7, 0], [0, 5]],                       # cyclic 35 (gcd 1)
+    [[16, 0], [0, 16]],                     # plain 2-D DFT
+    [[4, 1, 0], [0, 4, 1], [0, 0, 4]],      # one cycle of 64 in d = 3
+    [[6, 2, 0], [0, 6, 3], [0, 0, 6]],      # three cycles
+    [[3, 1, 2], [0, 2, 1], [1, 0, 4]],      # non-triangular 3-D
+    [[1, 0], [0, 1]],                       # m = 1
+    [[2, 1], [1, 1]],                       # unimodular, m = 1
+    [[9, 0, 3], [0, 12, 2], [0, 0, 10]],    # fast axis is not a maximal generator
+    [[64, 0], [0, 96]],                     # (32, 192): radix 3 with powers of two
+    [[2048, 16], [0, 2048]],                # Table 1 shape, cycles (16, 262144) -> too long
+]
+
+
+def _gpu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _plan_or_skip(M, batch, dtype):
+    try:
+        return pf.PatternFFT(M, batch, dtype)
+    except pf.PfftError as e:
+        if e.status == 5:  # PFFT_ERR_UNSUPPORTED: documented limits
+            pytest.skip(f"outside the kernels' limits: {e}")
+        raise
+
+
+@pytest.mark.parametrize("M", SMALL, ids=[str(i) for i in range(len(SMALL))])
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_small_patterns_full(M, dtype):
+    m = abs(L.det(M))
+    batch = 3
+    plan = _plan_or_skip(M, batch, dtype)
+    npdt = np.complex64 if dtype == torch.complex64 else np.complex128
+    c = SI.complex_normal(batch, m, seed=m % 97, dtype=npdt)
+    ref = oracle.pattern_fft(M, c)
+    got = plan.forward(_gpu(c)).cpu().numpy()
+    tol = TOL["c64" if dtype == torch.complex64 else "c128"]
+    assert rel_l2(got, ref) <= tol
+    back_ref = oracle.pattern_fft(M, ref, inverse=True)
+    back = plan.inverse(_gpu(ref.astype(npdt))).cpu().numpy()
+    assert rel_l2(back, back_ref) <= tol
+
+
+def test_small_2d_workload_seed0():
+    w = SI.WORKLOADS["small_2d"]
+    M, batch = w["M"], w["batch"]
+    m = abs(L.det(M))
+    c = SI.complex_normal(batch, m, w["seed"])
+    plan = pf.PatternFFT(M, batch)
+    got = plan.forward(_gpu(c))
+    ref = oracle.pattern_fft(M, c)
+    assert rel_l2(got.cpu().numpy(), ref) <= 1e-5
+    back = plan.inverse(got).cpu().numpy()
+    assert rel_l2(back, oracle.pattern_fft(M, ref, inverse=True)) <= 1e-5
+    assert rel_l2(back, c) <= 1e-5
+
+
+@pytest.mark.parametrize("M", [SI.M_SMALL_2D, [[6, 2], [-2, 6]], [[8, 2], [2, -4]], [[4, 1, 0], [0, 4, 1], [0, 0, 4]],
+                               [[6, 2, 0], [0, 6, 3], [0, 0, 6]], [[3, 1, 2], [0, 2, 1], [1, 0, 4]],
+                               [[9, 0, 3], [0, 12, 2], [0, 0, 10]], SI.M_BATCHED_2D, SI.M_AUTOGRAD_3D])
+def test_index_maps_bit_exact(M):
+    """The maps the kernels evaluate on the device are bijections onto the
+    boxes of the layout contract, agree with the host maps, and turn the
+    phase k^T M^{-1} y into sum_j lambda_j mu_j / n_j exactly (Theorem 1)."""
+    plan = pf.PatternFFT(M, 1)
+    m, d = plan.m, plan.d
+    Hbox = np.array(list(L.box_points(L.hnf(M)))) if m <= 1 << 16 else None
+    yin = plan.index_map(pf.PFFT_MAP_INPUT_BOX)
+    kout = plan.index_map(pf.PFFT_MAP_OUTPUT_BOX)
+    if Hbox is not None:
+        assert (yin == Hbox).all()
+        assert (kout == np.array(list(L.box_points(L.hnf(L.transpose(M)))))).all()
+    if plan.dM == 0:
+        return
+    lam = plan.index_map(pf.PFFT_MAP_INPUT_SNF)
+    mu = plan.index_map(pf.PFFT_MAP_OUTPUT_SNF)
+    n = [int(e) for e in plan.eps if e > 1]
+    flat = lambda v: np.ravel_multi_index(tuple(v.T), n)
+    dev_in = plan.device_index_map(pf.PFFT_MAP_INPUT_BOX).cpu().numpy()
+    dev_out = plan.device_index_map(pf.PFFT_MAP_OUTPUT_BOX).cpu().numpy()
+    slots = np.arange(m)
+    assert (np.sort(dev_in) == slots).all() and (np.sort(dev_out) == slots).all()
+    assert (dev_in[flat(lam)] == slots).all()
+    assert (dev_out[flat(mu)] == slots).all()
+    # exact phase identity on random pairs, against the adjugate numerator
+    A = np.array(L.adjugate(M), dtype=object)
+    sd = 1 if L.det(M) > 0 else -1
+    rng = np.random.default_rng(0)
+    for _ in range(300):
+        a, b = int(rng.integers(m)), int(rng.integers(m))
+        k, y = [int(x) for x in kout[a]], [int(x) for x in yin[b]]
+        num = sd * sum(k[i] * int(A[i][j]) * y[j] for i in range(d) for j in range(d)) % m
+        s = sum(int(lam[b][j]) * int(mu[a][j]) * (m // n[j]) for j in range(len(n))) % m
+        assert num == s
+
+
+def test_batched_2d_sampled_frequencies():
+    """Benchmark workload (M = [[4096,1024],[0,4096]], batch 8) in the launch
+    configuration the benchmark times; 4096 sampled frequencies of signal 0
+    and 512 of signal 7 by the direct FP64 sum; inverse on 1024 sampled slots."""
+    w = SI.WORKLOADS["batched_2d"]
+    M, batch = w["M"], w["batch"]
+    m = abs(L.det(M))
+    plan = pf.PatternFFT(M, batch)
+    c = SI.complex_normal(batch, m, w["seed"])
+    x = _gpu(c)
+    y = plan.forward(x)
+    yh = y.cpu().numpy()
+    for item, ns in ((0, 4096), (batch - 1, 512)):
+        slots = SI.sample_slots(m, ns)
+        ref = oracle.pattern_fft(M, c[item:item + 1], out_slots=slots)
+        assert rel_l2(yh[item:item + 1, slots], ref) <= 1e-5
+    # Parseval per signal (holds at every size)
+    assert np.allclose(np.linalg.norm(yh, axis=1), np.linalg.norm(c, axis=1), rtol=1e-5)
+    back = plan.inverse(y)
+    slots = SI.sample_slots(m, 1024, seed=7)
+    ref = oracle.pattern_fft(M, yh[2:3].astype(np.complex128), inverse=True, out_slots=slots)
+    assert rel_l2(back.cpu().numpy()[2:3, slots], ref) <= 1e-5
+    assert rel_l2(back.cpu().numpy(), c) <= 1e-5
+
+
+def test_autograd_3d_sampled_frequencies():
+    w = SI.WORKLOADS["autograd_3d"]
+    M, batch = w["M"], w["batch"]
+    m = abs(L.det(M))
+    plan = pf.PatternFFT(M, batch)
+    c = SI.complex_normal(batch, m, w["seed"])
+    y = plan.forward(_gpu(c)).cpu().numpy()
+    slots = SI.sample_slots(m, 2048)
+    ref = oracle.pattern_fft(M, c[1:2], out_slots=slots)
+    assert rel_l2(y[1:2, slots], ref) <= 1e-5
+    back = plan.inverse(_gpu(y)).cpu().numpy()
+    assert rel_l2(back, c) <= 1e-5
+
+
+def test_gpu_argument_errors():
+    plan = pf.PatternFFT(SI.M_SMALL_2D, 1)
+    x = torch.zeros(1, plan.m, dtype=torch.complex64, device="cuda")
+    with pytest.raises(pf.PfftError) as e:
+        pf.pfft_forward(plan._h, x.data_ptr(), x.data_ptr(), 0)
+    assert e.value.status == 1
+    with pytest.raises(ValueError):
+        plan.forward(x.to(torch.complex128))
+    with pytest.raises(ValueError):
+        plan.forward(x.cpu())
+
+
+def test_streams_and_repeat_calls_are_deterministic():
+    plan = pf.PatternFFT(SI.M_AUTOGRAD_3D, 1)
+    c = _gpu(SI.complex_normal(1, plan.m, 5))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a = plan.forward(c)
+        b = plan.forward(c)
+    s.synchronize()
+    assert torch.equal(a, b)

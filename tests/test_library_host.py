@@ -1,0 +1,109 @@
+"""CPU tests of the C-ABI library: it builds, loads and exports every entry
+point declared in include/pfft.h, and its exact host planner agrees with the
+oracle's independent lattice code.  No compute calls (no GPU here)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1107_5415_gb300 as pf
+from paper_1107_5415_gb300 import _capi
+from oracle import lattice as L
+import seeded_inputs as SI
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pfft.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:pfft_status|const char\*)\s+((?:pfft|pwt)_\w+)\(", src, re.M)))
+
+
+def test_header_declarations_match_binding():
+    assert _declared() == _capi.declared_symbols()
+
+
+def test_library_exports_every_declared_symbol():
+    path = pf.library_path()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T ((?:pfft|pwt)_\w+)$", out, re.M))
+    missing = [s for s in _declared() if s not in exported]
+    assert not missing, missing
+    lib = _capi.lib()
+    for s in _declared():
+        assert hasattr(lib, s)
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_hnf_matches_oracle(seed):
+    rng = np.random.default_rng(seed)
+    d = 1 + seed % 4
+    M = SI.random_regular_matrix(rng, d, 40, 10**7)
+    assert pf.pfft_hermite_normal_form(M).tolist() == L.hnf(M)
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_smith_form_properties(seed):
+    rng = np.random.default_rng(1000 + seed)
+    d = 1 + seed % 4
+    M = SI.random_regular_matrix(rng, d, 40, 10**7)
+    Q, eps, R = pf.pfft_smith_normal_form(M)
+    Q, R, eps = Q.tolist(), R.tolist(), [int(e) for e in eps]
+    E = [[eps[i] if i == j else 0 for j in range(d)] for i in range(d)]
+    assert L.matmul(L.matmul(Q, E), R) == [list(map(int, r)) for r in M]
+    assert abs(L.det(Q)) == 1 and abs(L.det(R)) == 1
+    assert all(eps[j + 1] % eps[j] == 0 for j in range(d - 1))
+    assert eps == L.elementary_divisors(M)
+
+
+def test_table1_cycles_from_library():
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_cycles.txt")
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        i, *cycles = map(int, line.split())
+        _, eps, _ = pf.pfft_smith_normal_form([[2048, i], [0, 2048]])
+        assert [int(e) for e in eps if e > 1] == cycles
+
+
+@pytest.mark.parametrize("M", [SI.M_SMALL_2D, SI.M_BATCHED_2D, SI.M_AUTOGRAD_3D, SI.M_WAVELET_2D])
+def test_workload_boxes(M):
+    H = pf.pfft_hermite_normal_form(M)
+    G = pf.pfft_hermite_normal_form(np.asarray(M).T)
+    assert np.prod(np.diag(H)) == np.prod(np.diag(G)) == abs(L.det(M))
+
+
+def test_host_errors():
+    with pytest.raises(pf.PfftError) as e:
+        pf.pfft_hermite_normal_form([[1, 2], [2, 4]])
+    assert e.value.status == 2  # PFFT_ERR_SINGULAR
+    with pytest.raises(pf.PfftError) as e:
+        pf.pfft_smith_normal_form([[1 << 25, 0], [0, 1]])
+    assert e.value.status == 3  # PFFT_ERR_OVERFLOW
+    with pytest.raises(pf.PfftError) as e:
+        pf.pfft_hermite_normal_form(np.eye(5, dtype=np.int64))
+    assert e.value.status == 1  # PFFT_ERR_ARG
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU path")
+def test_plan_without_gpu_fails_loudly():
+    with pytest.raises(pf.PfftError) as e:
+        pf.PatternFFT(SI.M_SMALL_2D, 1)
+    assert e.value.status == 7  # PFFT_ERR_CUDA: no CPU fallback
+    with pytest.raises(pf.PfftError):
+        pf.WaveletSplit(SI.M_WAVELET_2D, SI.wavelet_dilations(2))
+
+
+def test_plan_argument_errors():
+    with pytest.raises(pf.PfftError) as e:
+        pf.pfft_plan_create([[2, 1], [4, 2]], 1)
+    assert e.value.status == 2
+    with pytest.raises(pf.PfftError) as e:
+        pf.pfft_plan_create([[2, 0], [0, 2]], 0)
+    assert e.value.status == 1
+    with pytest.raises(pf.PfftError) as e:
+        pf.pwt_plan_create([[3, 0], [0, 4]], [[[2, 0], [0, 1]]], 0, 0.0, 1)
+    assert e.value.status == 4  # not integral (checked before the device)
