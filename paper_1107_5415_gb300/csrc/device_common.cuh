@@ -108,6 +108,64 @@ __device__ __forceinline__ int box_sum_slot(const BoxDesc& B, const int* a, cons
   return s;
 }
 
+
+// Slot of reduce(a + b) for two points a, b of the box, specialised on the
+// dimension.  Coordinate r of the sum lies in [0, 2 H_rr); the corrections of
+// the higher coordinates shift the lower ones by at most one diagonal each,
+// so every coordinate needs a bounded number of conditional steps.
+template <int DIM>
+__device__ __forceinline__ int box_sum_slot_t(const BoxDesc& B, const int* a, const int* b) {
+  if constexpr (DIM == 1) {
+    int y = a[0] + b[0];
+    if (y >= B.H[0][0]) y -= B.H[0][0];
+    return y;
+  } else if constexpr (DIM == 2) {
+    int y1 = a[1] + b[1];
+    const int c1 = y1 >= B.H[1][1];
+    y1 -= c1 * B.H[1][1];
+    int y0 = a[0] + b[0] - c1 * B.H[0][1];
+    y0 += (y0 < 0) * B.H[0][0];
+    y0 -= (y0 >= B.H[0][0]) * B.H[0][0];
+    return y0 * B.stride[0] + y1;
+  } else if constexpr (DIM == 3) {
+    int y2 = a[2] + b[2];
+    const int c2 = y2 >= B.H[2][2];
+    y2 -= c2 * B.H[2][2];
+    int y1 = a[1] + b[1] - c2 * B.H[1][2];
+    int y0 = a[0] + b[0] - c2 * B.H[0][2];
+    const int c1 = (y1 >= B.H[1][1]) - (y1 < 0);
+    y1 -= c1 * B.H[1][1];
+    y0 -= c1 * B.H[0][1];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      y0 += (y0 < 0) * B.H[0][0];
+      y0 -= (y0 >= B.H[0][0]) * B.H[0][0];
+    }
+    return y0 * B.stride[0] + y1 * B.stride[1] + y2;
+  } else {
+    return box_sum_slot(B, a, b);
+  }
+}
+
+// A table entry of a box point: TS = 2 (d <= 2) or 4 (d = 3, 4) int32,
+// fetched with one vector load.
+template <int TS>
+__device__ __forceinline__ void load_point(const int* __restrict__ tab, int idx, int* y) {
+  if constexpr (TS == 2) {
+    const int2 v = __ldg(reinterpret_cast<const int2*>(tab) + idx);
+    y[0] = v.x;
+    y[1] = v.y;
+    y[2] = 0;
+    y[3] = 0;
+  } else {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(tab) + idx);
+    y[0] = v.x;
+    y[1] = v.y;
+    y[2] = v.z;
+    y[3] = v.w;
+  }
+}
+
 // ------------------------------------------------------------- butterflies
 // In-register forward DFTs, X[k] = sum_n x[n] exp(-2 pi i n k / R).
 template <typename C>

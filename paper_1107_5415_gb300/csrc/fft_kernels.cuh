@@ -14,6 +14,29 @@ namespace pfft {
 // stride-R writes of the first radix stages free of bank conflicts.
 __device__ __forceinline__ int phys(int x) { return x + (x >> 4); }
 
+// Multiply v[r] by w^r, w = tw[base], r = 1..R-1.  The powers w^(2^b) come
+// from the table and w^r is their product over the set bits of r, so every
+// factor carries at most log2(R) - 1 rounded multiplications.
+template <typename C, int R>
+__device__ __forceinline__ void apply_twiddles(C* v, const C* __restrict__ tw, int base) {
+  constexpr int NB = (R > 16) ? 5 : (R > 8) ? 4 : (R > 4) ? 3 : (R > 2) ? 2 : 1;
+  C pw[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) pw[b] = __ldg(tw + (base << b));
+#pragma unroll
+  for (int r = 1; r < R; ++r) {
+    C f;
+    bool first = true;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (r & (1 << b)) {
+        f = first ? pw[b] : cmul(f, pw[b]);
+        first = false;
+      }
+    v[r] = cmul(v[r], f);
+  }
+}
+
 // One Stockham stage of radix R over every pencil of the tile.  Element
 // (pencil t, index i) lives at i*T + t (column pass, COLS) or t*L + i (row
 // pass).  Butterfly j of the axis reads i = base + (j + r a/R) sigma and,
@@ -49,10 +72,7 @@ __device__ __forceinline__ void run_stage(C* sm, const PassArgs& a, const StageD
       const int ebase = COLS ? base * a.T + t : t * a.L + base;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q][r] = sm[phys(ebase + (j + r * s.aR) * s.sigma * escale)];
-      if (s.Ns > 1) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], tw[k * r * s.twstep]);
-      }
+      if (s.Ns > 1) apply_twiddles<C, R>(v[q], tw, k * s.twstep);
       obase[q] = ebase + ((j - k) * R + k) * s.sigma * escale;
     }
   }
@@ -104,7 +124,10 @@ __device__ __forceinline__ C maybe_conj(C v, int c) {
   return c ? cconj(v) : v;
 }
 
-// Row pass: T rows of length nD per CTA, smem layout [t][e].
+// Row pass: T rows of length nD per CTA, smem layout [t][e].  Each thread
+// owns at most EPT elements of the tile: all of its global loads are issued
+// before the first shared-memory write (and all shared reads before the
+// first global store), so the loads of a thread are in flight together.
 template <typename C, int EPT, bool POW2>
 __global__ void __launch_bounds__(kMaxThreads, 1) row_pass_kernel(PassArgs a) {
   extern __shared__ unsigned char smem_raw[];
@@ -115,44 +138,72 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_pass_kernel(PassArgs a) {
   const int r0 = blockIdx.x * a.T;
   const int n = a.T * a.nD;
   const int d = a.d;
-
-  for (int w = threadIdx.x; w < n; w += blockDim.x) {
-    const int t = a.divnD.div(w);
-    const int e = w - t * a.nD;
-    const int row = r0 + t;
-    if (row >= a.LB) continue;
-    C v;
-    int sidx;
-    if (a.load_mode == MAP_BOX_H) {
-      v = in[box_sum_slot(a.boxH, a.Atab + row * d, a.Btab + e * d)];
-      sidx = e;
-    } else if (a.load_mode == MAP_WS) {
-      v = in[row * a.nD + e];
-      sidx = a.PIinv[e];
-    } else {
-      v = in[box_sum_slot(a.boxG, a.Ctab + row * d, a.Etab + e * d)];
-      sidx = a.PIinv[e];
+  const int nthr = blockDim.x;
+  constexpr int CH = EPT / 2;  // loads in flight per thread per chunk
+#pragma unroll
+  for (int k0 = 0; k0 < EPT; k0 += CH) {
+  C v[CH];
+  int sidx[CH];
+#pragma unroll
+  for (int kk = 0; kk < CH; ++kk) {
+    const int k = kk;
+    const int w = threadIdx.x + (k0 + k) * nthr;
+    sidx[k] = -1;
+    if (w < n) {
+      const int t = a.divnD.div(w);
+      const int e = w - t * a.nD;
+      const int row = r0 + t;
+      if (row < a.LB) {
+        if (a.load_mode == MAP_BOX_H) {
+          v[k] = __ldg(in + box_sum_slot(a.boxH, a.Atab + row * a.ts, a.Btab + e * a.ts));
+          sidx[k] = t * a.nD + e;
+        } else if (a.load_mode == MAP_WS) {
+          v[k] = __ldg(in + row * a.nD + e);
+          sidx[k] = t * a.nD + __ldg(a.PIinv + e);
+        } else {
+          v[k] = __ldg(in + box_sum_slot(a.boxG, a.Ctab + row * a.ts, a.Etab + e * a.ts));
+          sidx[k] = t * a.nD + __ldg(a.PIinv + e);
+        }
+      }
     }
-    sm[phys(t * a.nD + sidx)] = maybe_conj(v, a.conj_in);
+  }
+#pragma unroll
+  for (int k = 0; k < CH; ++k)
+    if (sidx[k] >= 0) sm[phys(sidx[k])] = maybe_conj(v[k], a.conj_in);
   }
   __syncthreads();
   run_all_stages<C, EPT, false, POW2>(sm, a, tw);
   using Rl = decltype(C::x);
   const Rl sc = Rl(a.scale);
-  for (int w = threadIdx.x; w < n; w += blockDim.x) {
-    const int t = a.divnD.div(w);
-    const int e = w - t * a.nD;
-    const int row = r0 + t;
-    if (row >= a.LB) continue;
-    if (a.store_mode == MAP_WS) {
-      out[row * a.nD + e] = sm[phys(t * a.nD + a.PIinv[e])];
-    } else if (a.store_mode == MAP_BOX_H) {
-      C v = maybe_conj(sm[phys(t * a.nD + e)], a.conj_out);
-      out[box_sum_slot(a.boxH, a.Atab + row * d, a.Btab + e * d)] = cscale(v, sc);
-    } else {
-      C v = maybe_conj(sm[phys(t * a.nD + a.PIinv[e])], a.conj_out);
-      out[box_sum_slot(a.boxG, a.Ctab + row * d, a.Etab + e * d)] = cscale(v, sc);
+#pragma unroll
+  for (int k0 = 0; k0 < EPT; k0 += CH) {
+  C v[CH];
+  int gidx[CH];
+#pragma unroll
+  for (int k = 0; k < CH; ++k) {
+    const int w = threadIdx.x + (k0 + k) * nthr;
+    gidx[k] = -1;
+    if (w < n) {
+      const int t = a.divnD.div(w);
+      const int e = w - t * a.nD;
+      const int row = r0 + t;
+      if (row < a.LB) {
+        if (a.store_mode == MAP_WS) {
+          v[k] = sm[phys(t * a.nD + __ldg(a.PIinv + e))];
+          gidx[k] = row * a.nD + e;
+        } else if (a.store_mode == MAP_BOX_H) {
+          v[k] = cscale(maybe_conj(sm[phys(t * a.nD + e)], a.conj_out), sc);
+          gidx[k] = box_sum_slot(a.boxH, a.Atab + row * a.ts, a.Btab + e * a.ts);
+        } else {
+          v[k] = cscale(maybe_conj(sm[phys(t * a.nD + __ldg(a.PIinv + e))], a.conj_out), sc);
+          gidx[k] = box_sum_slot(a.boxG, a.Ctab + row * a.ts, a.Etab + e * a.ts);
+        }
+      }
     }
+  }
+#pragma unroll
+  for (int k = 0; k < CH; ++k)
+    if (gidx[k] >= 0) out[gidx[k]] = v[k];
   }
 }
 
@@ -178,6 +229,7 @@ __device__ __forceinline__ int shear_index(const PassArgs& a, int j, const int* 
 
 // Column pass: all LB rows of T adjacent workspace columns per CTA, smem
 // layout [i][t].  The DFT runs over the (D-1) cycles inside the pencil.
+// Loads and stores are batched per thread as in the row pass.
 template <typename C, int EPT, bool POW2>
 __global__ void __launch_bounds__(kMaxThreads, 1) col_pass_kernel(PassArgs a) {
   extern __shared__ unsigned char smem_raw[];
@@ -188,60 +240,93 @@ __global__ void __launch_bounds__(kMaxThreads, 1) col_pass_kernel(PassArgs a) {
   const int p0 = blockIdx.x * a.T;
   const int n = a.T * a.LB;
   const int d = a.d;
+  const int nthr = blockDim.x;
   // blockDim.x is a multiple of T, so each thread keeps one column.
   const int tcol = a.divT.mod(threadIdx.x);
   int off[kMaxSub];
 #pragma unroll
   for (int s = 0; s < kMaxSub; ++s)
     off[s] = (s < a.nsub) ? int((int64_t(tcol) * a.alpha[s]) % a.sub_n[s]) : 0;
-  const int* etab = a.Etab + (p0 + tcol) * d;
-
-  if (a.load_mode == MAP_WS) {
-    for (int w = threadIdx.x; w < n; w += blockDim.x) {
-      const int i = a.divT.div(w);
-      sm[phys(i * a.T + tcol)] = maybe_conj(in[i * a.nD + p0 + tcol], a.conj_in);
+  int et[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) et[r] = (r < d) ? __ldg(a.Etab + (p0 + tcol) * a.ts + r) : 0;
+  constexpr int CH = EPT / 2;  // loads in flight per thread per chunk
+  const bool ws_in = a.load_mode == MAP_WS;
+#pragma unroll
+  for (int k0 = 0; k0 < EPT; k0 += CH) {
+  C v[CH];
+  int sidx[CH];
+#pragma unroll
+  for (int k = 0; k < CH; ++k) {
+    const int w = threadIdx.x + (k0 + k) * nthr;
+    sidx[k] = -1;
+    if (w < n) {
+      const int j = a.divT.div(w);
+      if (ws_in) {
+        v[k] = __ldg(in + j * a.nD + p0 + tcol);
+        sidx[k] = j * a.T + tcol;
+      } else {
+        const int i = shear_index(a, j, off);
+        v[k] = __ldg(in + box_sum_slot(a.boxG, a.Ctab + i * a.ts, et));
+        sidx[k] = i * a.T + tcol;
+      }
     }
-  } else {
-    for (int w = threadIdx.x; w < n; w += blockDim.x) {
-      const int i = shear_index(a, a.divT.div(w), off);
-      C v = in[box_sum_slot(a.boxG, a.Ctab + i * d, etab)];
-      sm[phys(i * a.T + tcol)] = maybe_conj(v, a.conj_in);
-    }
+  }
+#pragma unroll
+  for (int k = 0; k < CH; ++k)
+    if (sidx[k] >= 0) sm[phys(sidx[k])] = maybe_conj(v[k], a.conj_in);
   }
   __syncthreads();
   run_all_stages<C, EPT, true, POW2>(sm, a, tw);
   using Rl = decltype(C::x);
   const Rl sc = Rl(a.scale);
-  if (a.store_mode == MAP_WS) {
-    for (int w = threadIdx.x; w < n; w += blockDim.x) {
-      const int i = a.divT.div(w);
-      out[i * a.nD + p0 + tcol] = sm[phys(i * a.T + tcol)];
-    }
-  } else {
-    for (int w = threadIdx.x; w < n; w += blockDim.x) {
-      const int i = shear_index(a, a.divT.div(w), off);
-      C v = maybe_conj(sm[phys(i * a.T + tcol)], a.conj_out);
-      out[box_sum_slot(a.boxG, a.Ctab + i * d, etab)] = cscale(v, sc);
+  const bool ws_out = a.store_mode == MAP_WS;
+#pragma unroll
+  for (int k0 = 0; k0 < EPT; k0 += CH) {
+  C v[CH];
+  int gidx[CH];
+#pragma unroll
+  for (int k = 0; k < CH; ++k) {
+    const int w = threadIdx.x + (k0 + k) * nthr;
+    gidx[k] = -1;
+    if (w < n) {
+      const int j = a.divT.div(w);
+      if (ws_out) {
+        v[k] = sm[phys(j * a.T + tcol)];
+        gidx[k] = j * a.nD + p0 + tcol;
+      } else {
+        const int i = shear_index(a, j, off);
+        v[k] = cscale(maybe_conj(sm[phys(i * a.T + tcol)], a.conj_out), sc);
+        gidx[k] = box_sum_slot(a.boxG, a.Ctab + i * a.ts, et);
+      }
     }
   }
+#pragma unroll
+  for (int k = 0; k < CH; ++k)
+    if (gidx[k] >= 0) out[gidx[k]] = v[k];
+  }
+}
+
+// Allow the largest dynamic shared-memory size and prefer the maximum shared
+// carveout (more resident CTAs per SM).
+inline int configure_kernel(const void* k) {
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
+    return -1;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) return -1;
+  return 0;
 }
 
 template <typename C, int EPT, bool POW2>
 inline int launch_typed(const PassArgs& a, cudaStream_t s) {
   dim3 grid(a.groups, a.batch), block(a.nthreads);
-  if (a.cols) {
-    auto k = col_pass_kernel<C, EPT, POW2>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes) != cudaSuccess)
-      return -1;
-    k<<<grid, block, a.smem_bytes, s>>>(a);
-  } else {
-    auto k = row_pass_kernel<C, EPT, POW2>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes) != cudaSuccess)
-      return -1;
-    k<<<grid, block, a.smem_bytes, s>>>(a);
-  }
+  static const int row_ok = configure_kernel(reinterpret_cast<const void*>(row_pass_kernel<C, EPT, POW2>));
+  static const int col_ok = configure_kernel(reinterpret_cast<const void*>(col_pass_kernel<C, EPT, POW2>));
+  if (row_ok != 0 || col_ok != 0) return -1;
+  if (a.cols)
+    col_pass_kernel<C, EPT, POW2><<<grid, block, a.smem_bytes, s>>>(a);
+  else
+    row_pass_kernel<C, EPT, POW2><<<grid, block, a.smem_bytes, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
-
 
 }  // namespace pfft

@@ -33,6 +33,7 @@ struct pfft_plan_s {
   int* dtab = nullptr;
   void* tw = nullptr;
   void* ws = nullptr;
+  void* stw = nullptr;  // stage twiddle tables of the register-resident passes
   PassArgs rowp{}, colp{};
   Profiler prof;
 };
@@ -167,6 +168,36 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
   if (!set_stages(p, stg)) return PFFT_ERR_UNSUPPORTED;
   p.divT.init(uint32_t(T));
   p.divnD.init(uint32_t(P.nD));
+  p.logT = 0;
+  while ((1 << p.logT) < T) ++p.logT;
+  // register-resident power-of-two kernels (fft_fast.cuh)
+  {
+    const int Rm = P.dtype == PFFT_C64 ? 32 : 16;
+    const int L = p.L;
+    const bool pow2L = L >= Rm && (L & (L - 1)) == 0 && (T & (T - 1)) == 0;
+    p.fast = (p.pow2 && pow2L && P.d <= 3 && (!cols || P.D == 2) && T * L <= (P.dtype == PFFT_C64 ? 16384 : 8192)) ? 1 : 0;
+    if (p.fast) {
+      int lg = 0, lr = 0;
+      while ((1 << lg) < L) ++lg;
+      while ((1 << lr) < Rm) ++lr;
+      p.fast_nmain = lg / lr;
+      p.fast_tail = 1 << (lg - p.fast_nmain * lr);
+      p.nthreads = T * L / Rm;
+      // stage twiddle table: for main stage s (span Ns), w^(2^b) for k < Ns, b < log2 R
+      int off = 0, Ns = p.fast_tail;
+      for (int s = 0; s < p.fast_nmain; ++s) {
+        p.stw_off[s] = off;
+        off += Ns * lr;
+        Ns *= Rm;
+      }
+      p.stw_n = (off + 1) & ~1;
+      const int nel = T * L;
+      p.stw_smem_off = (nel + (nel >> 5) + 1) & ~1;
+      p.smem_bytes = int(size_t(p.stw_smem_off + p.stw_n) * elem_bytes(P.dtype));
+      if (p.nthreads <= kMaxThreads && p.smem_bytes <= 227 * 1024 && p.fast_nmain <= 4) return PFFT_OK;
+      p.fast = 0;
+    }
+  }
   p.nthreads = threads_for(p, ept);
   if (p.nthreads > kMaxThreads) return PFFT_ERR_UNSUPPORTED;
   const int nel = T * p.L;
@@ -334,12 +365,13 @@ static pfft_status plan_device(pfft_plan_s& P) {
     }
   }
   // index tables
-  std::vector<int> tab(size_t(2 * LB + 2 * nD) * d + 2 * nD);
+  const int ts = d <= 2 ? 2 : 4;  // int32 per entry, so that one vector load fetches a point
+  std::vector<int> tab(size_t(2 * LB + 2 * nD) * ts + 2 * nD, 0);
   int* Atab = tab.data();
-  int* Btab = Atab + size_t(LB) * d;
-  int* Ctab = Btab + size_t(nD) * d;
-  int* Etab = Ctab + size_t(LB) * d;
-  int* PIi = Etab + size_t(nD) * d;
+  int* Btab = Atab + size_t(LB) * ts;
+  int* Ctab = Btab + size_t(nD) * ts;
+  int* Etab = Ctab + size_t(LB) * ts;
+  int* PIi = Etab + size_t(nD) * ts;
   int* PIf = PIi + nD;
   std::vector<std::vector<i64>> glo(g.begin(), g.end() - 1), hlo(h.begin(), h.end() - 1);
   std::vector<i64> coef(std::max(D - 1, 0));
@@ -352,16 +384,16 @@ static pfft_status plan_device(pfft_plan_s& P) {
     auto a = combo(glo, coef, P.H);
     auto c = combo(hlo, coef, P.G);
     for (int k = 0; k < d; ++k) {
-      Atab[size_t(r) * d + k] = int(a[k]);
-      Ctab[size_t(r) * d + k] = int(c[k]);
+      Atab[size_t(r) * ts + k] = int(a[k]);
+      Ctab[size_t(r) * ts + k] = int(c[k]);
     }
   }
   for (int e = 0; e < nD; ++e) {
     auto b = combo({g[D - 1]}, {e}, P.H);
     auto c = combo({h[D - 1]}, {PIinv[e]}, P.G);
     for (int k = 0; k < d; ++k) {
-      Btab[size_t(e) * d + k] = int(b[k]);
-      Etab[size_t(e) * d + k] = int(c[k]);
+      Btab[size_t(e) * ts + k] = int(b[k]);
+      Etab[size_t(e) * ts + k] = int(c[k]);
     }
     PIi[e] = PIinv[e];
     PIf[e] = PI[e];
@@ -377,6 +409,58 @@ static pfft_status plan_device(pfft_plan_s& P) {
   if (cudaDeviceSynchronize() != cudaSuccess) return PFFT_ERR_CUDA;
 
   // pass descriptors (data pointers and modes are filled per call)
+  // arithmetic forms of PI and of the gather table (power-of-two cycles)
+  PassArgs arith;
+  std::memset(&arith, 0, sizeof(arith));
+  {
+    const i64 beta = posmod(P.MU[D - 1][d - 1], nD);
+    const i64 gg = beta == 0 ? nD : gcd64(beta, nD);
+    const i64 span = nD / gg;
+    auto lg2 = [](i64 v) { int l = 0; while ((i64(1) << l) < v) ++l; return (i64(1) << l) == v ? l : -1; };
+    if (lg2(gg) >= 0 && lg2(span) >= 0) {
+      arith.pi_arith = 1;
+      arith.pi_lg = lg2(gg);
+      arith.pi_lspan = lg2(span);
+      arith.pi_inv = int(span > 1 ? modinv(beta / gg, span) : 0);
+    }
+    // Btab[e] = (Z[e / H_ff], e mod H_ff) when g_D = e_f (the last input coordinate) and H_ff | nD
+    const i64 Hff = P.H(d - 1, d - 1);
+    bool unit = true;
+    std::vector<i64> ef(d, 0);
+    ef[d - 1] = 1;
+    {
+      std::vector<i64> gD = g[D - 1];
+      std::vector<i64> e1 = ef;
+      box_reduce(P.H, e1.data());
+      unit = (gD == e1);
+    }
+    const int lh = int(lg2(Hff));
+    if (unit && lh >= 0 && nD % Hff == 0 && nD / Hff <= 64 && d <= 3) {
+      arith.bz_arith = 1;
+      arith.bz_lh = lh;
+      for (i64 q = 0; q < nD / Hff; ++q) {
+        const int* b = Btab + size_t(q * Hff) * ts;
+        for (int r = 0; r + 1 < d; ++r) arith.bz[q][r] = b[r];
+        if (b[d - 1] != 0) arith.bz_arith = 0;
+      }
+      for (int e = 0; e < nD && arith.bz_arith; ++e) {  // exact check against the table
+        const int* b = Btab + size_t(e) * ts;
+        for (int r = 0; r + 1 < d; ++r)
+          if (b[r] != arith.bz[e >> lh][r]) arith.bz_arith = 0;
+        if (b[d - 1] != (e & ((1 << lh) - 1))) arith.bz_arith = 0;
+      }
+    }
+    if (arith.pi_arith)
+      for (int mu = 0; mu < nD; ++mu) {  // exact check against the table
+        const int span_i = 1 << arith.pi_lspan;
+        const int pos = ((mu & ((1 << arith.pi_lg) - 1)) << arith.pi_lspan) |
+                        (((mu >> arith.pi_lg) * arith.pi_inv) & (span_i - 1));
+        if (pos != PI[mu]) {
+          arith.pi_arith = 0;
+          break;
+        }
+      }
+  }
   const int budget = P.dtype == PFFT_C64 ? 8192 : 4096;
   for (PassArgs* p : {&P.rowp, &P.colp}) {
     std::memset(p, 0, sizeof(PassArgs));
@@ -385,9 +469,18 @@ static pfft_status plan_device(pfft_plan_s& P) {
     p->Ctab = Ctab - tab.data() + P.dtab;
     p->Etab = Etab - tab.data() + P.dtab;
     p->PIinv = PIi - tab.data() + P.dtab;
+    p->PI = PIf - tab.data() + P.dtab;
     p->tw = P.tw;
+    p->ts = ts;
     set_box(p->boxH, P.H);
     set_box(p->boxG, P.G);
+    p->pi_arith = arith.pi_arith;
+    p->pi_lg = arith.pi_lg;
+    p->pi_lspan = arith.pi_lspan;
+    p->pi_inv = arith.pi_inv;
+    p->bz_arith = arith.bz_arith;
+    p->bz_lh = arith.bz_lh;
+    std::memcpy(p->bz, arith.bz, sizeof(arith.bz));
     p->nsub = D - 1;
     for (int s = 0; s + 1 < D; ++s) {
       p->sub_n[s] = P.n[s];
@@ -401,6 +494,41 @@ static pfft_status plan_device(pfft_plan_s& P) {
     st = choose_and_configure(P.colp, P, true, 16, std::max(budget, LB));
     if (st != PFFT_OK) return st;
   }
+  // stage twiddle tables of the register-resident passes, gathered on the
+  // device from the FP64-built table: entry (s, k, b) = omega_{Ns R}^(k 2^b)
+  std::vector<int> idx;
+  std::vector<PassArgs*> fastp;
+  for (PassArgs* p : {&P.rowp, &P.colp})
+    if (p->fast && (p == &P.rowp || D >= 2)) fastp.push_back(p);
+  std::vector<size_t> base;
+  for (PassArgs* p : fastp) {
+    const int Rm = P.dtype == PFFT_C64 ? 32 : 16;
+    const int lr = Rm == 32 ? 5 : 4;
+    base.push_back(idx.size());
+    int Ns = p->fast_tail;
+    for (int s = 0; s < p->fast_nmain; ++s) {
+      const int NsR = Ns * Rm;
+      for (int k = 0; k < Ns; ++k)
+        for (int b = 0; b < lr; ++b) idx.push_back(int(((int64_t(k) << b) % NsR) * (nD / NsR)));
+      Ns *= Rm;
+    }
+    while (idx.size() - base.back() < size_t(p->stw_n)) idx.push_back(0);
+  }
+  if (!idx.empty()) {
+    int* didx = nullptr;
+    if (int e_ = device_alloc((void**)&didx, idx.size() * sizeof(int))) return pfft_status(e_);
+    if (int e_ = device_alloc(&P.stw, idx.size() * eb)) {
+      cudaFree(didx);
+      return pfft_status(e_);
+    }
+    cudaMemcpy(didx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
+    const int rc = launch_twiddle_gather(P.stw, P.tw, didx, int(idx.size()), P.dtype, 0);
+    const cudaError_t ce = cudaDeviceSynchronize();
+    cudaFree(didx);
+    if (rc != 0 || ce != cudaSuccess) return PFFT_ERR_CUDA;
+    for (size_t i = 0; i < fastp.size(); ++i)
+      fastp[i]->stw_g = static_cast<const char*>(P.stw) + base[i] * eb;
+  }
   return PFFT_OK;
 }
 
@@ -409,6 +537,7 @@ static void release(pfft_plan_s* P) {
   if (P->dtab) cudaFree(P->dtab);
   if (P->tw) cudaFree(P->tw);
   if (P->ws) cudaFree(P->ws);
+  if (P->stw) cudaFree(P->stw);
   delete P;
 }
 

@@ -49,10 +49,25 @@ struct PassArgs {
   int L;        // pencil length (row pass: nD; column pass: LB)
   int T;        // pencils per CTA
   int nD, LB, m, d;
+  int ts;       // int32 per table entry: 2 (d <= 2) or 4 (d = 3, 4)
   int cols;     // 1: column pass, 0: row pass
   int nstages;
   int cnt[14];  // stages per radix, in the order of kRadixOrder
   int pow2;     // all radices are powers of two
+  int fast;       // 1: use the register-resident power-of-two kernels (fft_fast.cuh)
+  int fast_tail;  // radix of the first stage (1 = none)
+  int fast_nmain; // number of main-radix stages
+  int logT;
+  // arithmetic column permutation (power-of-two nD):
+  // PI[mu] = ((mu & (g - 1)) << pi_lspan) | (((mu >> pi_lg) * pi_inv) & (span - 1))
+  int pi_arith, pi_lg, pi_lspan, pi_inv;
+  // arithmetic gather table: Btab[e] = (bz[e >> bz_lh][0..d-2], e & (2^bz_lh - 1))
+  int bz_arith, bz_lh;
+  int bz[64][3];
+  int stw_off[4];  // offset of each main stage's twiddles in the stage table
+  int stw_n;       // stage table length (complex, even)
+  int stw_smem_off;  // its place in shared memory (elements)
+  const void* stw_g;  // stage table in global memory
   StageDesc st[kMaxStages];
   FastDiv divT, divnD;
   int nthreads;
@@ -71,6 +86,7 @@ struct PassArgs {
   const int* Ctab;   // [LB]  box(G) point of sum_{j<D} mu_j h_j
   const int* Etab;   // [nD]  box(G) point of PIinv[pos] h_D   (indexed by position)
   const int* PIinv;  // [nD]  column position -> mu_D (or lambda_D)
+  const int* PI;     // [nD]  mu_D -> column position
   const void* tw;    // [nD]  omega_{nD}^t = exp(-2 pi i t / nD)
   BoxDesc boxH, boxG;
   // shear of the column pass: a run of consecutive output slots along the
@@ -84,6 +100,7 @@ struct PassArgs {
 // Host-side launcher (fft_kernels.cu).
 int launch_pass(const PassArgs& a, int dtype, cudaStream_t s);
 int launch_twiddles(void* tw, int nD, int dtype, cudaStream_t s);
+int launch_twiddle_gather(void* dst, const void* tw, const int* idx, int n, int dtype, cudaStream_t s);
 int launch_index_probe(const PassArgs& rowp, const PassArgs& colp, int which, int64_t* out,
                        cudaStream_t s);
 

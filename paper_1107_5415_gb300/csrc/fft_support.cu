@@ -32,6 +32,24 @@ int launch_twiddles(void* tw, int nD, int dtype, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// dst[i] = tw[idx[i]]: the stage tables of the register-resident passes.
+template <typename C>
+__global__ void twiddle_gather_kernel(C* dst, const C* tw, const int* idx, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = tw[idx[i]];
+}
+
+int launch_twiddle_gather(void* dst, const void* tw, const int* idx, int n, int dtype, cudaStream_t s) {
+  const int blk = 256, grd = (n + blk - 1) / blk;
+  if (dtype == 0)
+    twiddle_gather_kernel<float2><<<grd, blk, 0, s>>>(static_cast<float2*>(dst), static_cast<const float2*>(tw),
+                                                      idx, n);
+  else
+    twiddle_gather_kernel<double2><<<grd, blk, 0, s>>>(static_cast<double2*>(dst),
+                                                       static_cast<const double2*>(tw), idx, n);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 // Index probe: for every Smith coordinate vector (row-major, flattened as
 // row * nD + element), the box slot the transform kernels read (input map,
 // which = 0) or write (output map, which = 1), evaluated with the same
@@ -43,9 +61,9 @@ __global__ void index_probe_kernel(PassArgs a, const int* __restrict__ PI, int w
   const int row = int(w / a.nD), e = int(w - int64_t(row) * a.nD);
   int slot;
   if (which == 0)
-    slot = box_sum_slot(a.boxH, a.Atab + row * a.d, a.Btab + e * a.d);
+    slot = box_sum_slot(a.boxH, a.Atab + row * a.ts, a.Btab + e * a.ts);
   else
-    slot = box_sum_slot(a.boxG, a.Ctab + row * a.d, a.Etab + PI[e] * a.d);
+    slot = box_sum_slot(a.boxG, a.Ctab + row * a.ts, a.Etab + PI[e] * a.ts);
   out[w] = slot;
 }
 
