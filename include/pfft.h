@@ -199,6 +199,28 @@ pfft_status pwt_adjoint(pwt_plan p, const void* scaling, const void* const* wave
 
 pfft_status pwt_plan_destroy(pwt_plan p);
 
+/* The same decomposition as pwt_decompose for PFFT_C64 data, but without a
+ * plan and without allocating any device memory (the paper has no
+ * counterpart; this serves callers that cannot call cudaMalloc, e.g. code
+ * that runs under a device-memory budget or pool that forbids allocations,
+ * or that must not hit an allocation failure mid-run).  Arguments are those
+ * of pwt_plan_create and pwt_decompose; all pointers are caller-owned and
+ * `wavelets` is a host array of `levels` device pointers.
+ *   Scratch: the scaling parts between levels live in one fixed array of
+ *   2^21 complex64 values (16 MiB) that every GPU loading this library holds
+ *   until the process exits; (|det M| / 2) * batch must not exceed 2^20 when
+ *   levels > 1, else PFFT_ERR_OVERFLOW is returned and nothing runs.
+ *   The first call on a device looks the array up (cudaGetSymbolAddress), so
+ *   make that first call before any stream capture.  Every call on a device
+ *   shares the array: calls whose work overlaps on the GPU (other streams,
+ *   other host threads) race and must be serialised by the caller.  Nothing
+ *   in the array needs clearing: each call writes every element before it
+ *   reads it.  Phases are evaluated in single precision in the kernel
+ *   (equal to pwt_decompose within the complex64 tolerance). */
+pfft_status pwt_decompose_noalloc(int d, const int64_t* M, int levels, const int64_t* J, int symbol,
+                                  double eta, int64_t batch, const void* c_hat, void* scaling,
+                                  void* const* wavelets, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

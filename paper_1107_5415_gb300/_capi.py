@@ -66,6 +66,9 @@ _SIGS = {
     "pwt_reconstruct": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp), _vp, _vp]),
     "pwt_adjoint": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp), _vp, _vp]),
     "pwt_plan_destroy": (ctypes.c_int, [_vp]),
+    "pwt_decompose_noalloc": (ctypes.c_int, [ctypes.c_int, _i64p, ctypes.c_int, _i64p, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_int64, _vp, _vp, ctypes.POINTER(_vp),
+                                             _vp]),
 }
 
 
@@ -222,3 +225,17 @@ def pwt_adjoint(plan, scaling_ptr: int, wavelet_ptrs, c_hat_ptr: int, stream: in
 
 def pwt_plan_destroy(plan):
     _check(lib().pwt_plan_destroy(plan), "pwt_plan_destroy")
+
+
+def pwt_decompose_noalloc(M, Js, symbol: int, eta: float, batch: int, c_hat_ptr: int, scaling_ptr: int,
+                          wavelet_ptrs, stream: int):
+    """Plan-free decomposition that allocates no device memory (complex64)."""
+    d, (a, p) = _mat(M)
+    Ja = np.asarray(Js, dtype=np.int64)
+    levels = Ja.shape[0]
+    if Ja.shape != (levels, d, d):
+        raise ValueError("J must have shape [levels, d, d]")
+    ja, jp = _i64(Ja.reshape(-1))
+    arr = _ptr_array(wavelet_ptrs)
+    _check(lib().pwt_decompose_noalloc(d, p, levels, jp, int(symbol), float(eta), int(batch), c_hat_ptr,
+                                       scaling_ptr, arr, stream), "pwt_decompose_noalloc")

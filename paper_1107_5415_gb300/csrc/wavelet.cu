@@ -23,6 +23,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -152,7 +153,7 @@ __device__ Rl scaling_symbol(const LevelDesc& L, const int* h) {
   return sqrt(Rl(L.aJ)) * w;
 }
 
-template <typename C>
+template <typename C, bool TAB = true>
 __device__ __forceinline__ C wavelet_phase(const LevelDesc& L, const int* h) {
   long long t = 0;  // each product < 2^62; reduce term by term
 #pragma unroll
@@ -160,13 +161,20 @@ __device__ __forceinline__ C wavelet_phase(const LevelDesc& L, const int* h) {
     if (i < L.d) t += ((long long)h[i] * L.phw[i]) % L.q;
   t = (L.sM * t) % L.q;
   if (t < 0) t += L.q;
+  if constexpr (!TAB) {
+    // no tables: single-precision sincospi of the exactly reduced fraction t / q
+    using Rl = decltype(C::x);
+    float sn, cs;
+    sincospif(2.0f * (float(t) / float(L.q)), &sn, &cs);
+    return cmake<C>(Rl(cs), Rl(-sn));
+  }
   const C* lo = static_cast<const C*>(L.tab_lo);
   const C* hi = static_cast<const C*>(L.tab_hi);
   return cmul(hi[t >> kLoBits], lo[t & ((1 << kLoBits) - 1)]);
 }
 
 // mode 0: decompose c -> (d1, d2); 1: reconstruct; 2: adjoint.
-template <typename C, int MODE>
+template <typename C, int MODE, bool TAB = true>
 __global__ void __launch_bounds__(256) split_kernel(LevelDesc L, int batch, const C* __restrict__ cin,
                                                     C* __restrict__ cout, const C* __restrict__ d1in,
                                                     const C* __restrict__ d2in, C* __restrict__ d1out,
@@ -198,7 +206,7 @@ __global__ void __launch_bounds__(256) split_kernel(LevelDesc L, int batch, cons
     for (int r = 0; r < 4; ++r)
       if (r < L.d) slot1 += h1[r] * L.HM.stride[r];
     const Rl A0 = scaling_symbol<Rl>(L, g), A1 = scaling_symbol<Rl>(L, h1);
-    const C e0 = wavelet_phase<C>(L, g), e1 = wavelet_phase<C>(L, h1);
+    const C e0 = wavelet_phase<C, TAB>(L, g), e1 = wavelet_phase<C, TAB>(L, h1);
     const C B0 = cscale(e0, A1), B1 = cscale(e1, A0);
     const Rl r2 = Rl(0.70710678118654752440);
     const long long oM = (long long)b * L.mM, oN = (long long)b * L.mN;
@@ -557,4 +565,92 @@ extern "C" pfft_status pwt_reconstruct(pwt_plan p, const void* scaling, const vo
 extern "C" pfft_status pwt_adjoint(pwt_plan p, const void* scaling, const void* const* wavelets,
                                    void* c_hat, void* stream) {
   return synthesise(p, scaling, wavelets, c_hat, stream, 2);
+}
+
+// ---------------------------------------------------------------------------
+// Decomposition without any device allocation.
+//
+// Some callers cannot call cudaMalloc at all: code running under an external
+// memory budget or pool that forbids new device allocations, callers that
+// must not risk an allocation failure (or its implicit synchronisation) in
+// the middle of their work, and drivers that only own the buffers they pass
+// in.  For them the cascade keeps the scaling parts between levels in the
+// fixed array below instead of a plan-owned workspace, takes its per-level
+// parameters as kernel arguments and evaluates the wavelet phases in the
+// kernel instead of reading plan tables.  The array lives in every GPU that
+// loads this library until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocScratchElems = size_t(1) << 21;  // complex64 elements: 16 MiB
+__device__ __align__(256) float2 g_pwt_noalloc_scratch[kNoAllocScratchElems];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+float2* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side symbol is only a stand-in, not a device pointer).
+pfft_status noalloc_scratch(float2** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PFFT_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_pwt_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return PFFT_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<float2*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return PFFT_OK;
+}
+}  // namespace
+
+extern "C" pfft_status pwt_decompose_noalloc(int d, const int64_t* M, int levels, const int64_t* J, int symbol,
+                                             double eta, int64_t batch, const void* c_hat, void* scaling,
+                                             void* const* wavelets, void* stream) {
+  if (!M || !J || !c_hat || !scaling || !wavelets || d < 1 || d > 4 || levels < 1 || levels > 64 || batch < 1 ||
+      batch > (int64_t(1) << 20) || (symbol != PWT_DIRICHLET && symbol != PWT_DLVP) ||
+      (symbol == PWT_DLVP && !(eta > 0.0 && eta < 1.0)))
+    return PFFT_ERR_ARG;
+  for (int l = 0; l < levels; ++l)
+    if (!wavelets[l]) return PFFT_ERR_ARG;
+  pwt_plan_s P;  // host-side description only: plan_device is not called
+  P.d = d;
+  P.levels = levels;
+  P.symbol = symbol;
+  P.eta = eta;
+  P.batch = batch;
+  P.dtype = PFFT_C64;
+  pfft_status st;
+  try {
+    st = plan_levels(P, M, J);
+  } catch (const LatticeError& e) {
+    st = pfft_status(e.code);
+  }
+  if (st != PFFT_OK) return st;
+  // two ping-pong halves of the scratch hold the scaling parts of levels < L
+  const size_t half = kNoAllocScratchElems / 2;
+  if (levels > 1 && size_t(P.sizes[0] / 2) * size_t(batch) > half) return PFFT_ERR_OVERFLOW;
+  float2* scratch = nullptr;
+  if (levels > 1) {
+    st = noalloc_scratch(&scratch);
+    if (st != PFFT_OK) return st;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const void* cur = c_hat;
+  for (int l = 0; l < levels; ++l) {
+    void* d1 = (l == levels - 1) ? scaling : static_cast<void*>(scratch + (l & 1) * half);
+    const LevelDesc& L = P.lv[l];
+    const long long total = (long long)L.mN * batch;
+    long long grd = (total + 255) / 256;
+    if (grd > 152 * 64) grd = 152 * 64;
+    split_kernel<float2, 0, false><<<int(grd), 256, 0, s>>>(L, int(batch), static_cast<const float2*>(cur), nullptr,
+                                                             nullptr, nullptr, static_cast<float2*>(d1),
+                                                             static_cast<float2*>(wavelets[l]));
+    if (cudaGetLastError() != cudaSuccess) return PFFT_ERR_CUDA;
+    cur = d1;
+  }
+  return PFFT_OK;
 }
