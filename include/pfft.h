@@ -145,6 +145,11 @@ pfft_status pfft_inverse(pfft_plan p, const void* in, void* out, void* stream);
 
 pfft_status pfft_plan_destroy(pfft_plan p);
 
+/* Device status of a plan: synchronises `stream`, returns the status word the
+ * kernels set (PFFT_ERR_TIMEOUT when a bounded wait on an asynchronous copy
+ * gave up; PFFT_OK otherwise) and clears it. */
+pfft_status pfft_last_device_status(pfft_plan p, void* stream);
+
 /* Per-kernel timing of a plan's launches (CUDA events recorded on the
  * launching stream around each kernel).  enable != 0 starts recording and
  * clears the totals.  pfft_profile_read writes up to `cap` entries: kernel

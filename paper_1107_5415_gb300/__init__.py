@@ -23,7 +23,7 @@ from . import _capi
 from ._capi import (PFFT_C64, PFFT_C128, PFFT_MAP_INPUT_BOX, PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_BOX,
                     PFFT_MAP_OUTPUT_SNF, PWT_DIRICHLET, PWT_DLVP, PfftError, pfft_device_index_map,
                     pfft_forward, pfft_hermite_normal_form, pfft_index_map, pfft_inverse, pfft_plan_create,
-                    pfft_plan_destroy, pfft_plan_info, pfft_profile_enable, pfft_profile_read,
+                    pfft_last_device_status, pfft_plan_destroy, pfft_plan_info, pfft_profile_enable, pfft_profile_read,
                     pfft_smith_normal_form, pwt_adjoint, pwt_decompose, pwt_plan_create, pwt_plan_destroy,
                     pwt_plan_info, pwt_reconstruct)
 
@@ -32,7 +32,7 @@ __all__ = [
     "PfftError", "PFFT_C64", "PFFT_C128", "PWT_DIRICHLET", "PWT_DLVP",
     "PFFT_MAP_INPUT_BOX", "PFFT_MAP_OUTPUT_BOX", "PFFT_MAP_INPUT_SNF", "PFFT_MAP_OUTPUT_SNF",
     "pfft_plan_create", "pfft_plan_info", "pfft_index_map", "pfft_device_index_map", "pfft_forward",
-    "pfft_inverse", "pfft_plan_destroy", "pfft_profile_enable", "pfft_profile_read",
+    "pfft_inverse", "pfft_plan_destroy", "pfft_last_device_status", "pfft_profile_enable", "pfft_profile_read",
     "pfft_hermite_normal_form", "pfft_smith_normal_form", "pwt_plan_create", "pwt_plan_info",
     "pwt_decompose", "pwt_reconstruct", "pwt_adjoint", "pwt_plan_destroy", "library_path",
 ]
@@ -107,6 +107,10 @@ class PatternFFT:
         out = torch.empty(self.m, dtype=torch.int64, device=device or "cuda")
         pfft_device_index_map(self._h, which, out.data_ptr(), _stream(None))
         return out
+
+    def check_device_status(self, stream=None):
+        """Raise PfftError if a kernel of this plan recorded a device-side failure."""
+        pfft_last_device_status(self._h, _stream(stream))
 
     def profile(self, enable: bool = True):
         pfft_profile_enable(self._h, enable)

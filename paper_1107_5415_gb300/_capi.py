@@ -54,6 +54,7 @@ _SIGS = {
     "pfft_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "pfft_inverse": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "pfft_plan_destroy": (ctypes.c_int, [_vp]),
+    "pfft_last_device_status": (ctypes.c_int, [_vp, _vp]),
     "pfft_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pfft_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_char_p), _i64p,
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int,
@@ -163,6 +164,11 @@ def pfft_forward(plan, in_ptr: int, out_ptr: int, stream: int):
 
 def pfft_inverse(plan, in_ptr: int, out_ptr: int, stream: int):
     _check(lib().pfft_inverse(plan, in_ptr, out_ptr, stream), "pfft_inverse")
+
+
+def pfft_last_device_status(plan, stream: int):
+    """Status word of the plan's kernels (0 = ok); raises on a non-zero status."""
+    _check(lib().pfft_last_device_status(plan, stream), "pfft_last_device_status")
 
 
 def pfft_plan_destroy(plan):

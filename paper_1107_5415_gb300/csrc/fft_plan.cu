@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -34,6 +35,8 @@ struct pfft_plan_s {
   void* tw = nullptr;
   void* ws = nullptr;
   void* stw = nullptr;  // stage twiddle tables of the register-resident passes
+  int* runs = nullptr;  // bulk-copy runs of the row pass
+  int* status = nullptr;  // device status word
   PassArgs rowp{}, colp{};
   Profiler prof;
 };
@@ -403,6 +406,8 @@ static pfft_status plan_device(pfft_plan_s& P) {
     return PFFT_ERR_CUDA;
   const size_t eb = elem_bytes(P.dtype);
   if (int e_ = device_alloc((void**)&P.tw, size_t(nD) * eb)) return pfft_status(e_);
+  if (int e_ = device_alloc((void**)&P.status, sizeof(int))) return pfft_status(e_);
+  cudaMemset(P.status, 0, sizeof(int));
   if (launch_twiddles(P.tw, nD, P.dtype, 0) != 0) return PFFT_ERR_CUDA;
   if (D >= 2)
     if (int e_ = device_alloc(&P.ws, size_t(P.m) * P.batch * eb)) return pfft_status(e_);
@@ -472,6 +477,7 @@ static pfft_status plan_device(pfft_plan_s& P) {
     p->PI = PIf - tab.data() + P.dtab;
     p->tw = P.tw;
     p->ts = ts;
+    p->status = P.status;
     set_box(p->boxH, P.H);
     set_box(p->boxG, P.G);
     p->pi_arith = arith.pi_arith;
@@ -514,6 +520,50 @@ static pfft_status plan_device(pfft_plan_s& P) {
     }
     while (idx.size() - base.back() < size_t(p->stw_n)) idx.push_back(0);
   }
+  // runs of consecutive box slots along each row, for bulk-copy staging
+  if (P.rowp.fast && P.rowp.T == 1 && D >= 2 && (P.m * elem_bytes(P.dtype)) % 16 == 0) {
+    std::vector<std::array<int, 4>> runs;
+    int maxr = 0;
+    bool ok = true;
+    std::vector<std::vector<std::array<int, 4>>> per(LB);
+    std::vector<i64> y(d);
+    auto slot_of = [&](int r, int e) {
+      for (int k = 0; k < d; ++k) y[k] = i64(Atab[size_t(r) * ts + k]) + Btab[size_t(e) * ts + k];
+      box_reduce(P.H, y.data());
+      return box_slot(P.H, y.data());
+    };
+    const int align = int(16 / elem_bytes(P.dtype));  // elements per 16 bytes
+    for (int r = 0; r < LB && ok; ++r) {
+      i64 start = slot_of(r, 0), prev = start;
+      int e0 = 0;
+      for (int e = 1; e <= nD && ok; ++e) {
+        const i64 s = e < nD ? slot_of(r, e) : -2;
+        if (s != prev + 1) {
+          const int len = e - e0;
+          if (e0 % align || start % align || len % align) ok = false;
+          per[r].push_back({e0, int(start), len, 0});
+          e0 = e;
+          start = s;
+        }
+        prev = s;
+      }
+      maxr = std::max<int>(maxr, int(per[r].size()));
+      if (maxr > 64 || maxr > P.rowp.nthreads) ok = false;
+    }
+    if (ok) {
+      std::vector<int> flat(size_t(LB) * maxr * 4, 0);
+      for (int r = 0; r < LB; ++r)
+        for (size_t j = 0; j < per[r].size(); ++j)
+          for (int k = 0; k < 4; ++k) flat[(size_t(r) * maxr + j) * 4 + k] = per[r][j][k];
+      if (int e_ = device_alloc((void**)&P.runs, flat.size() * sizeof(int))) return pfft_status(e_);
+      cudaMemcpy(P.runs, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice);
+      P.rowp.tma = 1;
+      P.rowp.runs = P.runs;
+      P.rowp.nruns = maxr;
+      P.rowp.bar_smem_off = (P.rowp.smem_bytes + 15) & ~15;
+      P.rowp.smem_bytes = P.rowp.bar_smem_off + 16;
+    }
+  }
   if (!idx.empty()) {
     int* didx = nullptr;
     if (int e_ = device_alloc((void**)&didx, idx.size() * sizeof(int))) return pfft_status(e_);
@@ -538,6 +588,8 @@ static void release(pfft_plan_s* P) {
   if (P->tw) cudaFree(P->tw);
   if (P->ws) cudaFree(P->ws);
   if (P->stw) cudaFree(P->stw);
+  if (P->runs) cudaFree(P->runs);
+  if (P->status) cudaFree(P->status);
   delete P;
 }
 
@@ -689,4 +741,16 @@ extern "C" pfft_status pfft_profile_read(pfft_plan p, const char** names, int64_
                                          int cap, int* n) {
   if (!p) return PFFT_ERR_ARG;
   return p->prof.read(names, launches, ms, cap, n) ? PFFT_OK : PFFT_ERR_CUDA;
+}
+
+extern "C" pfft_status pfft_last_device_status(pfft_plan p, void* stream) {
+  if (!p) return PFFT_ERR_ARG;
+  if (!p->status) return PFFT_OK;
+  int v = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&v, p->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return PFFT_ERR_CUDA;
+  if (v != 0) cudaMemsetAsync(p->status, 0, sizeof(int), s);
+  return pfft_status(v);
 }

@@ -68,6 +68,12 @@ struct PassArgs {
   int stw_n;       // stage table length (complex, even)
   int stw_smem_off;  // its place in shared memory (elements)
   const void* stw_g;  // stage table in global memory
+  // bulk-copy staging of the row pass (fft_tma.cuh)
+  int tma;            // 1: use row_tma_kernel
+  const int* runs;    // [LB][nruns] int4 (element offset, box slot, length, 0)
+  int nruns;
+  int bar_smem_off;   // byte offset of the mbarrier in shared memory
+  int* status;        // device status word (PFFT_ERR_TIMEOUT on a timed-out wait)
   StageDesc st[kMaxStages];
   FastDiv divT, divnD;
   int nthreads;

@@ -139,6 +139,7 @@ def test_batched_2d_sampled_frequencies():
     # Parseval per signal (holds at every size)
     assert np.allclose(np.linalg.norm(yh, axis=1), np.linalg.norm(c, axis=1), rtol=1e-5)
     back = plan.inverse(y)
+    plan.check_device_status()  # no bounded wait timed out
     slots = SI.sample_slots(m, 1024, seed=7)
     ref = oracle.pattern_fft(M, yh[2:3].astype(np.complex128), inverse=True, out_slots=slots)
     assert rel_l2(back.cpu().numpy()[2:3, slots], ref) <= 1e-5
