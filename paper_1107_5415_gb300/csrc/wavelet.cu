@@ -15,15 +15,23 @@
 // with B the indicator of [-1/2, 1/2] taking 1/2 on the boundary (Dirichlet,
 // equal to the case formula of Section 6.2), or, for the de la Vallee Poussin
 // reading, A(h) = sqrt|det J| w(N^{-T} h) with B(s) = clamp(((1+eta)/2-|s|)/eta, 0, 1).
-// N^{-T} h = J^T M^{-T} h is formed from the exact integer numerators
-// adj(M^T) h over |det M|.  Wavelet symbol B(h) = A(h + N^T l1)
+// Because J^T Z^d has index 2 it is the kernel of n -> v.n mod 2 for one
+// parity vector v, and both B's are partitions of unity over integer shifts,
+//     w(t) = (1 + prod_j U_j(t_j)) / 2,   U_j(t) = sum_n B(t + n) (-1)^(v_j n),
+// so each coordinate needs at most three candidate shifts and no product over
+// lattice points.  On the fibre partner (t shifted by the class not in
+// J^T Z^d) the product changes sign: w(h1) = 1 - w(h0).  N^{-T} h is formed
+// from exact integer numerators K h over |det M|, K = sign(det M) J^T adj(M^T),
+// reduced mod 2 |det M| (U_j has period 2).  Wavelet symbol B(h) = A(h + N^T l1)
 // exp(-2 pi i h^T N^{-1} z), with h^T N^{-1} z = h^T M^{-1} (J z) read from a
-// two-level table of exp(-2 pi i t / |det M|) built in FP64.
+// two-level table of exp(-2 pi i t / |det M|) built in FP64; on the partner
+// the phase changes sign (l1^T z = 1/2 mod 1).
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <new>
 #include <vector>
 
@@ -53,114 +61,81 @@ struct LevelDesc {
   long long phw[4];      // adj(M) (J z): phase numerator of h is sM * h . phw mod q
   int symbol;
   double eta;
+  long long K[16];       // sign(det M) J^T adj(M^T): N^{-T} h = K h / q
+  int K32[16];           // the same in int32 when `small`
+  int small;             // |K h| < 2^30 for every box point h: int32 arithmetic
+  int vpar[4];           // parity vector of J^T Z^d
+  FastDiv div2q;         // division by 2q (int32 path)
+  int off2q;             // multiple of 2q that makes K h non-negative (int32 path)
+  int ph32[4];           // sign(det M) adj(M) (J z) mod q (int32 path)
+  FastDiv divq;          // division by q (int32 path)
+  int offq;              // multiple of q that makes ph32 . h non-negative
   const void* tab_lo;    // exp(-2 pi i t / q), t < 2^kLoBits
   const void* tab_hi;    // exp(-2 pi i (t << kLoBits) / q)
 };
 
-__device__ __forceinline__ long long floordiv_ll(long long a, long long b) {  // b > 0
-  long long q = a / b;
-  if ((a % b) != 0 && a < 0) --q;
-  return q;
-}
-
-template <typename Rl>
-__device__ Rl scaling_symbol(const LevelDesc& L, const int* h) {
+// Periodised weight w(N^{-T} h) of the point h (see the header comment);
+// the fibre partner has weight 1 - w.
+template <typename Rl, bool SMALL>
+__device__ __forceinline__ Rl fibre_weight(const LevelDesc& L, const int* h) {
+  using I = typename std::conditional<SMALL, int, long long>::type;
   const int d = L.d;
-  const long long q = L.q;
-  long long v[4], u[4];
+  const I q = I(L.q);
+  Rl prod = Rl(1);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     if (j >= d) break;
-    long long p = 0;
+    I t;  // numerator of (N^{-T} h)_j mod 2, in [0, 2q)
+    if constexpr (SMALL) {
+      int acc = L.off2q;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (i < d) p += L.adjMT[j * d + i] * (long long)h[i];
-    p *= L.sM;
-    u[j] = p - q * floordiv_ll(2 * p + q, 2 * q);  // centred numerator, M^{-T} h mod 1
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (j >= d) break;
-    long long s = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (i < d) s += (long long)L.J[i * d + j] * u[i];
-    v[j] = s;  // N^{-T} h = v / q
-  }
-  // candidate integer shifts per coordinate with their weights
-  int ncand[4];
-  long long nval[4][3];
-  Rl wts[4][3];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    ncand[j] = 1;
-    if (j >= d) continue;
-    const long long r = floordiv_ll(2 * v[j] + q, 2 * q);
-    const long long c = v[j] - q * r;  // in [-q/2, q/2)
-    ncand[j] = 0;
-    if (L.symbol == PWT_DIRICHLET) {
-      if (2 * c == -q) {
-        nval[j][0] = -r;
-        wts[j][0] = Rl(0.5);
-        nval[j][1] = -r + 1;
-        wts[j][1] = Rl(0.5);
-        ncand[j] = 2;
-      } else {
-        nval[j][0] = -r;
-        wts[j][0] = Rl(1);
-        ncand[j] = 1;
-      }
+      for (int i = 0; i < 4; ++i)
+        if (i < d) acc += L.K32[j * d + i] * h[i];
+      t = L.div2q.mod(acc);
     } else {
-      const Rl eta = Rl(L.eta);
+      long long acc = 0;
 #pragma unroll
-      for (int o = -1; o <= 1; ++o) {
-        const Rl s = Rl(c + (long long)o * q) / Rl(q);
-        Rl b = (Rl(0.5) * (Rl(1) + eta) - (s < 0 ? -s : s)) / eta;
-        if (b > Rl(0)) {
-          nval[j][ncand[j]] = -r + o;
-          wts[j][ncand[j]] = b < Rl(1) ? b : Rl(1);
-          ++ncand[j];
-        }
+      for (int i = 0; i < 4; ++i)
+        if (i < d) acc += L.K[j * d + i] * (long long)h[i];
+      t = acc % (2 * q);
+      if (t < 0) t += 2 * q;
+    }
+    Rl U = Rl(0);
+#pragma unroll
+    for (int n = 0; n >= -2; --n) {  // shifts with |t/q + n| possibly < 1
+      const I sn = t + I(n) * q;
+      const I an = sn < 0 ? -sn : sn;
+      Rl b;
+      if (L.symbol == PWT_DIRICHLET) {
+        b = (2 * an < q) ? Rl(1) : (2 * an == q) ? Rl(0.5) : Rl(0);
+      } else {
+        const Rl eta = Rl(L.eta);
+        b = (Rl(0.5) * (Rl(1) + eta) - Rl(an) / Rl(q)) / eta;
+        b = b < Rl(0) ? Rl(0) : (b > Rl(1) ? Rl(1) : b);
       }
-      if (ncand[j] == 0) return Rl(0);
+      U += ((L.vpar[j] & n) & 1) ? -b : b;
     }
+    prod *= U;
   }
-  Rl w = 0;
-  int idx[4] = {0, 0, 0, 0};
-  for (;;) {
-    bool member = true;  // n in J^T Z^d  <=>  adj(J^T) n = 0 mod |det J|
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (i >= d) break;
-      long long s = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (j < d) s += L.adjJT[i * d + j] * nval[j][idx[j]];
-      if (s % L.aJ != 0) member = false;
-    }
-    if (member) {
-      Rl p = 1;
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (j < d) p *= wts[j][idx[j]];
-      w += p;
-    }
-    int j = d - 1;
-    while (j >= 0 && ++idx[j] == ncand[j]) idx[j--] = 0;
-    if (j < 0) break;
-  }
-  if (L.symbol == PWT_DIRICHLET) return sqrt(Rl(L.aJ) * w);
-  return sqrt(Rl(L.aJ)) * w;
+  return Rl(0.5) * (Rl(1) + prod);
 }
 
-template <typename C, bool TAB = true>
+template <typename C, bool TAB = true, bool SMALL = false>
 __device__ __forceinline__ C wavelet_phase(const LevelDesc& L, const int* h) {
-  long long t = 0;  // each product < 2^62; reduce term by term
+  long long t = 0;
+  if constexpr (SMALL) {
+    int acc = L.offq;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-    if (i < L.d) t += ((long long)h[i] * L.phw[i]) % L.q;
-  t = (L.sM * t) % L.q;
-  if (t < 0) t += L.q;
+    for (int i = 0; i < 4; ++i)
+      if (i < L.d) acc += L.ph32[i] * h[i];
+    t = L.divq.mod(acc);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)  // each product < 2^62; reduce term by term
+      if (i < L.d) t += ((long long)h[i] * L.phw[i]) % L.q;
+    t = (L.sM * t) % L.q;
+    if (t < 0) t += L.q;
+  }
   if constexpr (!TAB) {
     // no tables: single-precision sincospi of the exactly reduced fraction t / q
     using Rl = decltype(C::x);
@@ -173,18 +148,17 @@ __device__ __forceinline__ C wavelet_phase(const LevelDesc& L, const int* h) {
   return cmul(hi[t >> kLoBits], lo[t & ((1 << kLoBits) - 1)]);
 }
 
-// mode 0: decompose c -> (d1, d2); 1: reconstruct; 2: adjoint.
-template <typename C, int MODE, bool TAB = true>
+// mode 0: decompose c -> (d1, d2); 1: reconstruct; 2: adjoint.  One thread
+// per fibre g (grid-stride over the slots of one signal, blockIdx.y = signal).
+template <typename C, int MODE, bool TAB = true, bool SMALL = false>
 __global__ void __launch_bounds__(256) split_kernel(LevelDesc L, int batch, const C* __restrict__ cin,
                                                     C* __restrict__ cout, const C* __restrict__ d1in,
                                                     const C* __restrict__ d2in, C* __restrict__ d1out,
                                                     C* __restrict__ d2out) {
   using Rl = decltype(C::x);
-  const long long total = (long long)L.mN * batch;
-  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
-       w += (long long)gridDim.x * blockDim.x) {
-    const int b = int(w / L.mN);
-    const int gs = int(w - (long long)b * L.mN);
+  (void)batch;
+  const int b = blockIdx.y;
+  for (int gs = blockIdx.x * blockDim.x + threadIdx.x; gs < L.mN; gs += gridDim.x * blockDim.x) {
     int g[4] = {0, 0, 0, 0}, h1[4] = {0, 0, 0, 0};
     int s = gs;
     for (int r = L.d - 1; r >= 0; --r) {
@@ -205,21 +179,32 @@ __global__ void __launch_bounds__(256) split_kernel(LevelDesc L, int batch, cons
 #pragma unroll
     for (int r = 0; r < 4; ++r)
       if (r < L.d) slot1 += h1[r] * L.HM.stride[r];
-    const Rl A0 = scaling_symbol<Rl>(L, g), A1 = scaling_symbol<Rl>(L, h1);
-    const C e0 = wavelet_phase<C, TAB>(L, g), e1 = wavelet_phase<C, TAB>(L, h1);
-    const C B0 = cscale(e0, A1), B1 = cscale(e1, A0);
+    const Rl w0 = fibre_weight<Rl, SMALL>(L, g);
+    const Rl w1 = Rl(1) - w0;
+    Rl A0, A1;
+    if (L.symbol == PWT_DIRICHLET) {
+      A0 = sqrt(Rl(2) * w0);
+      A1 = sqrt(Rl(2) * w1);
+    } else {
+      A0 = Rl(1.41421356237309504880) * w0;
+      A1 = Rl(1.41421356237309504880) * w1;
+    }
+    // B(h0) = A(h1) e(h0), B(h1) = A(h0) e(h1), e(h1) = -e(h0)
+    const C e0 = wavelet_phase<C, TAB, SMALL>(L, g);
     const Rl r2 = Rl(0.70710678118654752440);
     const long long oM = (long long)b * L.mM, oN = (long long)b * L.mN;
     if (MODE == 0) {
       const C c0 = cin[oM + slot0], c1 = cin[oM + slot1];
       d1out[oN + gs] = cscale(cadd(cscale(c0, A0), cscale(c1, A1)), r2);
-      d2out[oN + gs] = cscale(cadd(cmul(cconj(B0), c0), cmul(cconj(B1), c1)), r2);
+      // conj(B0) c0 + conj(B1) c1 = conj(e0) (A1 c0 - A0 c1)
+      d2out[oN + gs] = cscale(cmul(cconj(e0), csub(cscale(c0, A1), cscale(c1, A0))), r2);
     } else {
       const C a = d1in[oN + gs], bb = d2in[oN + gs];
       const Rl S = A0 * A0 + A1 * A1;
       const Rl fac = (MODE == 1) ? Rl(1.41421356237309504880) / S : r2;
-      cout[oM + slot0] = cscale(cadd(cscale(a, A0), cmul(B0, bb)), fac);
-      cout[oM + slot1] = cscale(cadd(cscale(a, A1), cmul(B1, bb)), fac);
+      const C eb = cmul(e0, bb);
+      cout[oM + slot0] = cscale(cadd(cscale(a, A0), cscale(eb, A1)), fac);
+      cout[oM + slot1] = cscale(csub(cscale(a, A1), cscale(eb, A0)), fac);
     }
   }
 }
@@ -240,24 +225,35 @@ __global__ void phase_table_kernel(C* lo, C* hi, long long q, int nhi) {
   }
 }
 
-template <typename C>
-static int launch_split(const LevelDesc& L, int batch, int mode, const void* cin, void* cout,
-                        const void* d1in, const void* d2in, void* d1out, void* d2out, cudaStream_t s) {
-  const long long total = (long long)L.mN * batch;
+template <typename C, bool SMALL>
+static void launch_split_t(const LevelDesc& L, int batch, int mode, const void* cin, void* cout,
+                           const void* d1in, const void* d2in, void* d1out, void* d2out, cudaStream_t s) {
   const int blk = 256;
-  long long grd = (total + blk - 1) / blk;
-  if (grd > 152 * 64) grd = 152 * 64;
+  long long gx = (L.mN + blk - 1) / blk;
+  const long long cap = (152LL * 16 + batch - 1) / batch;  // about 16 resident waves of CTAs in total
+  if (gx > cap) gx = cap;
+  if (gx < 1) gx = 1;
+  dim3 grid((unsigned)gx, (unsigned)batch);
   auto c = [](const void* p) { return static_cast<const C*>(p); };
   auto m = [](void* p) { return static_cast<C*>(p); };
   if (mode == 0)
-    split_kernel<C, 0><<<int(grd), blk, 0, s>>>(L, batch, c(cin), nullptr, nullptr, nullptr, m(d1out),
-                                                 m(d2out));
+    split_kernel<C, 0, true, SMALL><<<grid, blk, 0, s>>>(L, batch, c(cin), nullptr, nullptr, nullptr, m(d1out),
+                                                          m(d2out));
   else if (mode == 1)
-    split_kernel<C, 1><<<int(grd), blk, 0, s>>>(L, batch, nullptr, m(cout), c(d1in), c(d2in), nullptr,
-                                                 nullptr);
+    split_kernel<C, 1, true, SMALL><<<grid, blk, 0, s>>>(L, batch, nullptr, m(cout), c(d1in), c(d2in), nullptr,
+                                                          nullptr);
   else
-    split_kernel<C, 2><<<int(grd), blk, 0, s>>>(L, batch, nullptr, m(cout), c(d1in), c(d2in), nullptr,
-                                                 nullptr);
+    split_kernel<C, 2, true, SMALL><<<grid, blk, 0, s>>>(L, batch, nullptr, m(cout), c(d1in), c(d2in), nullptr,
+                                                          nullptr);
+}
+
+template <typename C>
+static int launch_split(const LevelDesc& L, int batch, int mode, const void* cin, void* cout, const void* d1in,
+                        const void* d2in, void* d1out, void* d2out, cudaStream_t s) {
+  if (L.small)
+    launch_split_t<C, true>(L, batch, mode, cin, cout, d1in, d2in, d1out, d2out, s);
+  else
+    launch_split_t<C, false>(L, batch, mode, cin, cout, d1in, d2in, d1out, d2out, s);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -424,6 +420,54 @@ static pfft_status plan_levels(pwt_plan_s& P, const int64_t* Mv, const int64_t* 
     }
     L.symbol = P.symbol;
     L.eta = P.eta;
+    {
+      // K = sign(det M) J^T adj(M^T): numerators of N^{-T} h over q
+      IMat JT = J.transpose();
+      IMat K = matmul(JT, adjMT);
+      const int sM = detM < 0 ? -1 : 1;
+      i128 bound = 0;
+      for (int r = 0; r < d; ++r) {
+        i128 row = 0;
+        for (int c = 0; c < d; ++c) {
+          L.K[r * d + c] = sM * K(r, c);
+          const i64 a = K(r, c) < 0 ? -K(r, c) : K(r, c);
+          row += (i128)a * HM(c, c);
+        }
+        if (row > bound) bound = row;
+      }
+      if (bound >= ((i128)1 << 60)) return PFFT_ERR_OVERFLOW;
+      const i128 twoq = 2 * (i128)q;
+      // phase vector sign(det M) adj(M) (J z) reduced mod q into (-q, q)
+      i128 pbound = 0;
+      for (int i = 0; i < d; ++i) {
+        const i64 v = (L.sM < 0 ? -1 : 1) * (L.phw[i] % q);
+        L.ph32[i] = int(v);
+        pbound += (i128)(v < 0 ? -v : v) * HM(i, i);
+      }
+      L.small = (bound < ((i128)1 << 29) && twoq < ((i128)1 << 29) && pbound < ((i128)1 << 29)) ? 1 : 0;
+      if (L.small) {
+        for (int k = 0; k < d * d; ++k) L.K32[k] = int(L.K[k]);
+        L.div2q.init(uint32_t(2 * q));
+        L.off2q = int(((bound / twoq) + 1) * twoq);
+        L.divq.init(uint32_t(q));
+        L.offq = int(((pbound / q) + 1) * q);
+      }
+      // parity vector: v . n = 0 mod 2 exactly on J^T Z^d (its columns span it)
+      bool found = false;
+      for (int v = 1; v < (1 << d) && !found; ++v) {
+        bool ok = true;
+        for (int c = 0; c < d && ok; ++c) {
+          i64 s2 = 0;
+          for (int r = 0; r < d; ++r) s2 += ((v >> r) & 1) * JT(r, c);
+          if (posmod(s2, 2) != 0) ok = false;
+        }
+        if (ok) {
+          for (int r = 0; r < d; ++r) L.vpar[r] = (v >> r) & 1;
+          found = true;
+        }
+      }
+      if (!found) return PFFT_ERR_UNSUPPORTED;
+    }
     P.lv.push_back(L);
     P.boxes.push_back(HM);
     P.sizes.push_back(q);
@@ -643,12 +687,18 @@ extern "C" pfft_status pwt_decompose_noalloc(int d, const int64_t* M, int levels
   for (int l = 0; l < levels; ++l) {
     void* d1 = (l == levels - 1) ? scaling : static_cast<void*>(scratch + (l & 1) * half);
     const LevelDesc& L = P.lv[l];
-    const long long total = (long long)L.mN * batch;
-    long long grd = (total + 255) / 256;
-    if (grd > 152 * 64) grd = 152 * 64;
-    split_kernel<float2, 0, false><<<int(grd), 256, 0, s>>>(L, int(batch), static_cast<const float2*>(cur), nullptr,
-                                                             nullptr, nullptr, static_cast<float2*>(d1),
-                                                             static_cast<float2*>(wavelets[l]));
+    long long gx = (L.mN + 255) / 256;
+    const long long cap = (152LL * 16 + batch - 1) / batch;
+    if (gx > cap) gx = cap;
+    dim3 grid(unsigned(gx < 1 ? 1 : gx), unsigned(batch));
+    const float2* src = static_cast<const float2*>(cur);
+    float2* o1 = static_cast<float2*>(d1);
+    float2* o2 = static_cast<float2*>(wavelets[l]);
+    if (L.small)
+      split_kernel<float2, 0, false, true><<<grid, 256, 0, s>>>(L, int(batch), src, nullptr, nullptr, nullptr, o1, o2);
+    else
+      split_kernel<float2, 0, false, false><<<grid, 256, 0, s>>>(L, int(batch), src, nullptr, nullptr, nullptr, o1,
+                                                                  o2);
     if (cudaGetLastError() != cudaSuccess) return PFFT_ERR_CUDA;
     cur = d1;
   }
