@@ -39,13 +39,15 @@ METRIC = "pattern-FFT points/s & % of HBM roofline vs plain FP32 form at rel-L2â
 WORKLOAD = "batched_2d"
 BYTES_PER_POINT_PASS = 16  # complex64: 8 B read + 8 B write per point and pass
 KERNELS = ("row_pass", "col_pass")
+WAVELET = "wavelet_2d"
 
 
-def workload_desc():
+def workload_desc(batch=None):
     w = SI.WORKLOADS[WORKLOAD]
+    b = batch or w["batch"]
     return {"workload": "batched 2-D pattern FFT, forward + inverse", "M": w["M"], "m": 1 << 24,
-            "batch": w["batch"], "cycles": [1024, 16384], "input": "complex64, re/im i.i.d. N(0,1), seed 1",
-            "l2": "inputs larger than L2 (1 GiB per buffer), no flush"}
+            "batch": b, "cycles": [1024, 16384], "input": "complex64, re/im i.i.d. N(0,1), seed 1",
+            "l2": f"inputs larger than L2 ({b * 128} MiB per buffer), no flush"}
 
 
 def measured_peaks():
@@ -196,6 +198,43 @@ def oracle_sample_rate(target_s: float, threads: int | None = None):
     return S / dt, dt, S, nthreads
 
 
+def bench_wavelet(pf, torch, peaks_hbm, steps=20, warmup=3):
+    """12-level split cascade on M_0 = 2^10 [[1,1],[-1,1]] (2^21 points), batch 16,
+    Dirichlet and de la Vallee Poussin symbols, coefficients resident in HBM.
+    Reports input points per second of the whole cascade and the roofline of
+    its dominant kernel (the first split level: 8 B read + 8 B written per
+    input point, from a one-level plan timed with CUDA events)."""
+    w = SI.WORKLOADS[WAVELET]
+    M, batch, levels = w["M"], w["batch"], w["levels"]
+    out = {"workload": "12-level wavelet split cascade, M0 = 2^10 [[1,1],[-1,1]], J alternating "
+                       "[[1,1],[-1,1]] / [[1,-1],[1,1]], batch 16, complex64", "m": 1 << 21, "batch": batch}
+    stream = torch.cuda.current_stream()
+    for sym, name in ((pf.PWT_DIRICHLET, "dirichlet"), (pf.PWT_DLVP, "dlvp")):
+        for L in (levels, 1):
+            plan = pf.WaveletSplit(M, SI.wavelet_dilations(L), sym, 0.125, batch)
+            c = torch.from_numpy(SI.complex_normal(batch, plan.sizes[0], w["seed"])).cuda()
+            for _ in range(warmup):
+                plan.decompose(c)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                plan.decompose(c)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            pts = plan.sizes[0] * batch
+            if L == levels:
+                out[name] = {"value": pts / (ms * 1e-3), "unit": "points/s", "ms": ms}
+            else:
+                gbs = 16 * pts / (ms * 1e-3) / 1e9
+                out[name]["level1_kernel"] = {"avg_ms": ms, "achieved_gbs": gbs, "frac": gbs / peaks_hbm,
+                                              "alg_bytes_per_launch": 16 * pts}
+            plan.close()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -228,7 +267,7 @@ def run_native(args):
     rank, world, local = dist_setup(args.gpus)
     dev = torch.device("cuda", torch.cuda.current_device())
     w = SI.WORKLOADS[WORKLOAD]
-    M, batch = w["M"], w["batch"]
+    M, batch = w["M"], args.batch or w["batch"]
     plan = pf.PatternFFT(M, batch)
     m = plan.m
     host = torch.from_numpy(SI.complex_normal(batch, m, w["seed"] + 1000 * rank))
@@ -264,6 +303,14 @@ def run_native(args):
     ms_max, points = aggregate(ms, points_local, world)
     value = points / (ms_max * 1e-3)
 
+    wavelet = None if args.no_wavelet else bench_wavelet(pf, torch, peaks_hbm=float(measured_peaks()[0]["hbm_gbs"]))
+    if args.no_e2e:
+        e2e_value, e2e_ms = None, None
+        plan.close()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "points/s", "ms_per_step": ms_max,
+                              "kernels": prof, "wavelet": wavelet, "note": "profiling run (no e2e)"}), flush=True)
+        return 0
     # end to end through the public API with host buffers (pinned), per step:
     # H2D of the input, forward + inverse, D2H of the result
     hin = host.pin_memory()
@@ -318,6 +365,7 @@ def run_native(args):
             "compulsory_frac": (BYTES_PER_POINT_PASS * points_local / (ms * 1e-3) / 1e9) / peak,
             "kernels": kernels,
             "cpu_baseline": cpu,
+            "wavelet": wavelet,
             "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": int(x.numel() * 8),
                     "d2h_bytes_per_step": int(z.numel() * 8)},
             "gpu_launches": 4 * args.steps,
@@ -339,6 +387,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-wavelet", action="store_true", help="skip the wavelet cascade measurement")
+    ap.add_argument("--batch", type=int, default=0, help="override the workload batch (profiling runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
