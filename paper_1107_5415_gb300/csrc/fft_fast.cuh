@@ -238,6 +238,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_fast_kernel(PassArgs a) {
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = cconj(v[k]);
   }
+  if (a.fs_na > 1 && a.load_mode == MAP_WS) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = cmul(v[k], fs_twiddle<C>(a, rowc, p + P * k));
+  }
   cp_async_wait_all();
   __syncthreads();
   fast_pencil_dft<C, R, false>(v, sm, stw, a, p, t * L, 1, L);
@@ -246,6 +250,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_fast_kernel(PassArgs a) {
   const Rl sc = Rl(a.scale);
   if (a.store_mode == MAP_WS) {
     C* dst = out + row * a.nD;
+    if (a.fs_na > 1) {
+#pragma unroll
+      for (int k = 0; k < R; ++k) v[k] = cmul(v[k], fs_twiddle<C>(a, row, p + P * k));
+    }
 #pragma unroll
     for (int k = 0; k < R; ++k) dst[col_pos(a, p + P * k)] = v[k];
   } else {

@@ -119,10 +119,6 @@ __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ t
 #undef PFFT_REGION
 }
 
-template <typename C>
-__device__ __forceinline__ C maybe_conj(C v, int c) {
-  return c ? cconj(v) : v;
-}
 
 // Row pass: T rows of length nD per CTA, smem layout [t][e].  Each thread
 // owns at most EPT elements of the tile: all of its global loads are issued
@@ -158,8 +154,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_pass_kernel(PassArgs a) {
           v[k] = __ldg(in + box_sum_slot(a.boxH, a.Atab + row * a.ts, a.Btab + e * a.ts));
           sidx[k] = t * a.nD + e;
         } else if (a.load_mode == MAP_WS) {
+          const int mu = __ldg(a.PIinv + e);
           v[k] = __ldg(in + row * a.nD + e);
-          sidx[k] = t * a.nD + __ldg(a.PIinv + e);
+          if (a.fs_na > 1) v[k] = cmul(maybe_conj(v[k], a.conj_in), fs_twiddle<C>(a, row, mu));
+          else v[k] = maybe_conj(v[k], a.conj_in);
+          sidx[k] = t * a.nD + mu;
         } else {
           v[k] = __ldg(in + box_sum_slot(a.boxG, a.Ctab + row * a.ts, a.Etab + e * a.ts));
           sidx[k] = t * a.nD + __ldg(a.PIinv + e);
@@ -169,7 +168,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_pass_kernel(PassArgs a) {
   }
 #pragma unroll
   for (int k = 0; k < CH; ++k)
-    if (sidx[k] >= 0) sm[phys(sidx[k])] = maybe_conj(v[k], a.conj_in);
+    if (sidx[k] >= 0) sm[phys(sidx[k])] = (a.load_mode == MAP_WS) ? v[k] : maybe_conj(v[k], a.conj_in);
   }
   __syncthreads();
   run_all_stages<C, EPT, false, POW2>(sm, a, tw);
@@ -189,7 +188,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_pass_kernel(PassArgs a) {
       const int row = r0 + t;
       if (row < a.LB) {
         if (a.store_mode == MAP_WS) {
-          v[k] = sm[phys(t * a.nD + __ldg(a.PIinv + e))];
+          const int mu = __ldg(a.PIinv + e);
+          v[k] = sm[phys(t * a.nD + mu)];
+          if (a.fs_na > 1) v[k] = cmul(v[k], fs_twiddle<C>(a, row, mu));
           gidx[k] = row * a.nD + e;
         } else if (a.store_mode == MAP_BOX_H) {
           v[k] = cscale(maybe_conj(sm[phys(t * a.nD + e)], a.conj_out), sc);

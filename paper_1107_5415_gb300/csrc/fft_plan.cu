@@ -28,7 +28,11 @@ struct pfft_plan_s {
   std::vector<int> n;                   // their lengths, ascending
   std::vector<std::vector<i64>> LAM;    // D rows: lambda_j(y) = LAM_j . y mod n_j
   std::vector<std::vector<i64>> MU;     // D rows: mu_j(k) = MU_j . k mod n_j
-  int nD = 1, LB = 1;
+  int nD = 1, LB = 1;      // row length and number of rows of the logical LB x nD array
+  std::vector<int> pen;     // column-pass pencil axes (row-major), product LB
+  int fs_na = 1;            // four-step split of a long last cycle: n = fs_na * nD
+  i64 fs_N = 1;             // the full length of the last cycle
+  void* fs_tab = nullptr;   // exp(-2 pi i t / fs_N), two-level table
   // device state
   int device = 0;
   int* dtab = nullptr;
@@ -162,9 +166,9 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
   } else {
     p.L = P.LB;
     int sigma = 1;
-    for (int s = P.D - 2; s >= 0; --s) {  // pencil axes n_1..n_{D-1}, last fastest
-      if (!axis_stages(stg, P.n[s], sigma, P.nD)) return PFFT_ERR_UNSUPPORTED;
-      sigma *= P.n[s];
+    for (int s = int(P.pen.size()) - 1; s >= 0; --s) {  // pencil axes, last fastest
+      if (!axis_stages(stg, P.pen[s], sigma, P.nD)) return PFFT_ERR_UNSUPPORTED;
+      sigma *= P.pen[s];
     }
     p.groups = P.nD / T;
   }
@@ -178,7 +182,7 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
     const int Rm = P.dtype == PFFT_C64 ? 32 : 16;
     const int L = p.L;
     const bool pow2L = L >= Rm && (L & (L - 1)) == 0 && (T & (T - 1)) == 0;
-    p.fast = (p.pow2 && pow2L && P.d <= 3 && (!cols || P.D == 2) && T * L <= (P.dtype == PFFT_C64 ? 16384 : 8192)) ? 1 : 0;
+    p.fast = (p.pow2 && pow2L && P.d <= 3 && (!cols || P.pen.size() == 1) && T * L <= (P.dtype == PFFT_C64 ? 16384 : 8192)) ? 1 : 0;
     if (p.fast) {
       int lg = 0, lr = 0;
       while ((1 << lg) < L) ++lg;
@@ -298,7 +302,33 @@ static pfft_status plan_host(pfft_plan_s& P, int d, const int64_t* Mv) {
       ++P.D;
     }
   if (P.D > 3) return PFFT_ERR_UNSUPPORTED;
-  P.nD = P.D ? P.n[P.D - 1] : 1;
+  P.fs_N = P.D ? P.n[P.D - 1] : 1;
+  P.fs_na = 1;
+  P.nD = int(P.fs_N);
+  P.pen.assign(P.n.begin(), P.n.end() - (P.D ? 1 : 0));
+  // A last cycle longer than one row tile is split four-step style,
+  // n = n_a n_b with lambda = lambda_a + n_a lambda_b: the row pass runs the
+  // length-n_b DFTs (twiddle exp(-2 pi i lambda_a mu_b / n) between the passes)
+  // and lambda_a becomes one more pencil axis of the column pass.
+  const int row_max = P.dtype == PFFT_C64 ? 16384 : 8192;
+  if (P.fs_N > row_max) {
+    const i64 other = P.m / P.fs_N;
+    std::vector<int> rad;
+    int best = 0;
+    for (i64 nb = row_max; nb >= 2; --nb) {
+      if (P.fs_N % nb) continue;
+      const i64 na = P.fs_N / nb;
+      if (!factor_radices(int(nb), rad) || na > row_max || !factor_radices(int(na), rad)) continue;
+      if (other * na > row_max) continue;
+      best = int(nb);
+      break;
+    }
+    if (!best) return PFFT_ERR_UNSUPPORTED;
+    P.nD = best;
+    P.fs_na = int(P.fs_N / best);
+    P.pen.push_back(P.fs_na);
+  }
+  if (P.pen.size() > size_t(kMaxSub)) return PFFT_ERR_UNSUPPORTED;
   P.LB = int(P.m / P.nD);
   return PFFT_OK;
 }
@@ -352,12 +382,35 @@ static pfft_status plan_device(pfft_plan_s& P) {
         return PFFT_ERR_OVERFLOW;
     }
   const int nD = P.nD, LB = P.LB;
+  const int na = P.fs_na;
+  const int npen = int(P.pen.size());
+  // Row (A, B) and column (C, E) generator lists of the logical LB x nD array:
+  //   row index  = flatten(lambda_1..lambda_{D-1}[, lambda_a]),  element = lambda_b
+  //   col index  = flatten(mu_1..mu_{D-1}[, mu_a]),              position of mu_b
+  // with lambda_D = lambda_a + n_a lambda_b and mu_D = mu_b + n_b mu_a when the
+  // last cycle is split (n_a > 1); otherwise lambda_b = lambda_D, mu_b = mu_D.
+  std::vector<std::vector<i64>> genA(g.begin(), g.end() - 1), genC(h.begin(), h.end() - 1);
+  std::vector<i64> gB = g[D - 1], hE = h[D - 1];
+  if (na > 1) {
+    genA.push_back(g[D - 1]);
+    std::vector<i64> hb(d), gb(d);
+    for (int k = 0; k < d; ++k) {
+      hb[k] = h[D - 1][k] * nD;  // n_b h_D (|h| < 2^31, n_b <= 2^14)
+      gb[k] = g[D - 1][k] * na;  // n_a g_D
+    }
+    box_reduce(P.G, hb.data());
+    box_reduce(P.H, gb.data());
+    genC.push_back(hb);
+    gB = gb;
+  }
   // column permutation PI for the column pass (see fft_plan.hpp)
   std::vector<int> PI(nD), PIinv(nD);
   std::vector<int> alpha(3, 0);
   {
-    i64 beta = posmod(P.MU[D - 1][d - 1], nD);
+    const i64 cf = posmod(P.MU[D - 1][d - 1], P.fs_N);  // mu_D of the fastest output coordinate
+    i64 beta = cf % nD;
     for (int j = 0; j + 1 < D; ++j) alpha[j] = int(posmod(P.MU[j][d - 1], P.n[j]));
+    if (na > 1) alpha[npen - 1] = int((cf / nD) % na);
     const i64 gg = beta == 0 ? nD : gcd64(beta, nD);
     const i64 span = nD / gg;
     const i64 inv = span > 1 ? modinv(beta / gg, span) : 0;
@@ -376,24 +429,23 @@ static pfft_status plan_device(pfft_plan_s& P) {
   int* Etab = Ctab + size_t(LB) * ts;
   int* PIi = Etab + size_t(nD) * ts;
   int* PIf = PIi + nD;
-  std::vector<std::vector<i64>> glo(g.begin(), g.end() - 1), hlo(h.begin(), h.end() - 1);
-  std::vector<i64> coef(std::max(D - 1, 0));
+  std::vector<i64> coef(npen);
   for (int r = 0; r < LB; ++r) {
     int x = r;
-    for (int j = D - 2; j >= 0; --j) {
-      coef[j] = x % P.n[j];
-      x /= P.n[j];
+    for (int j = npen - 1; j >= 0; --j) {
+      coef[j] = x % P.pen[j];
+      x /= P.pen[j];
     }
-    auto a = combo(glo, coef, P.H);
-    auto c = combo(hlo, coef, P.G);
+    auto a = combo(genA, coef, P.H);
+    auto c = combo(genC, coef, P.G);
     for (int k = 0; k < d; ++k) {
       Atab[size_t(r) * ts + k] = int(a[k]);
       Ctab[size_t(r) * ts + k] = int(c[k]);
     }
   }
   for (int e = 0; e < nD; ++e) {
-    auto b = combo({g[D - 1]}, {e}, P.H);
-    auto c = combo({h[D - 1]}, {PIinv[e]}, P.G);
+    auto b = combo({gB}, {e}, P.H);
+    auto c = combo({hE}, {PIinv[e]}, P.G);
     for (int k = 0; k < d; ++k) {
       Btab[size_t(e) * ts + k] = int(b[k]);
       Etab[size_t(e) * ts + k] = int(c[k]);
@@ -409,8 +461,13 @@ static pfft_status plan_device(pfft_plan_s& P) {
   if (int e_ = device_alloc((void**)&P.status, sizeof(int))) return pfft_status(e_);
   cudaMemset(P.status, 0, sizeof(int));
   if (launch_twiddles(P.tw, nD, P.dtype, 0) != 0) return PFFT_ERR_CUDA;
-  if (D >= 2)
+  if (npen >= 1)
     if (int e_ = device_alloc(&P.ws, size_t(P.m) * P.batch * eb)) return pfft_status(e_);
+  if (na > 1) {  // exp(-2 pi i t / n) for t < n, as lo[t & 2047] * hi[t >> 11]
+    const int nhi = int((P.fs_N + 2047) >> 11);
+    if (int e_ = device_alloc(&P.fs_tab, size_t(2048 + nhi) * eb)) return pfft_status(e_);
+    if (launch_phase_tables(P.fs_tab, P.fs_N, nhi, P.dtype, 0) != 0) return PFFT_ERR_CUDA;
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) return PFFT_ERR_CUDA;
 
   // pass descriptors (data pointers and modes are filled per call)
@@ -487,16 +544,20 @@ static pfft_status plan_device(pfft_plan_s& P) {
     p->bz_arith = arith.bz_arith;
     p->bz_lh = arith.bz_lh;
     std::memcpy(p->bz, arith.bz, sizeof(arith.bz));
-    p->nsub = D - 1;
-    for (int s = 0; s + 1 < D; ++s) {
-      p->sub_n[s] = P.n[s];
-      p->sub_div[s].init(uint32_t(P.n[s]));
+    p->nsub = npen;
+    for (int s = 0; s < npen; ++s) {
+      p->sub_n[s] = P.pen[s];
+      p->sub_div[s].init(uint32_t(P.pen[s]));
       p->alpha[s] = alpha[s];
     }
+    p->fs_na = na;
+    p->fs_div.init(uint32_t(na));
+    p->fs_lo = P.fs_tab;
+    p->fs_hi = P.fs_tab ? static_cast<const char*>(P.fs_tab) + size_t(2048) * eb : nullptr;
   }
   pfft_status st = choose_and_configure(P.rowp, P, false, 64, std::max(budget, nD));
   if (st != PFFT_OK) return st;
-  if (D >= 2) {
+  if (npen >= 1) {
     st = choose_and_configure(P.colp, P, true, 16, std::max(budget, LB));
     if (st != PFFT_OK) return st;
   }
@@ -505,7 +566,7 @@ static pfft_status plan_device(pfft_plan_s& P) {
   std::vector<int> idx;
   std::vector<PassArgs*> fastp;
   for (PassArgs* p : {&P.rowp, &P.colp})
-    if (p->fast && (p == &P.rowp || D >= 2)) fastp.push_back(p);
+    if (p->fast && (p == &P.rowp || npen >= 1)) fastp.push_back(p);
   std::vector<size_t> base;
   for (PassArgs* p : fastp) {
     const int Rm = P.dtype == PFFT_C64 ? 32 : 16;
@@ -521,7 +582,7 @@ static pfft_status plan_device(pfft_plan_s& P) {
     while (idx.size() - base.back() < size_t(p->stw_n)) idx.push_back(0);
   }
   // runs of consecutive box slots along each row, for bulk-copy staging
-  if (P.rowp.fast && P.rowp.T == 1 && D >= 2 && (P.m * elem_bytes(P.dtype)) % 16 == 0) {
+  if (P.rowp.fast && P.rowp.T == 1 && npen >= 1 && (P.m * elem_bytes(P.dtype)) % 16 == 0) {
     std::vector<std::array<int, 4>> runs;
     int maxr = 0;
     bool ok = true;
@@ -588,6 +649,7 @@ static void release(pfft_plan_s* P) {
   if (P->tw) cudaFree(P->tw);
   if (P->ws) cudaFree(P->ws);
   if (P->stw) cudaFree(P->stw);
+  if (P->fs_tab) cudaFree(P->fs_tab);
   if (P->runs) cudaFree(P->runs);
   if (P->status) cudaFree(P->status);
   delete P;
@@ -708,7 +770,7 @@ static pfft_status transform(pfft_plan p, const void* in, void* out, void* strea
                                                                                        : PFFT_ERR_CUDA;
   }
   const int ci = inverse ? 1 : 0;
-  if (p->D == 1) {
+  if (p->pen.empty()) {
     return run_pass(p, p->rowp, inverse ? MAP_BOX_G : MAP_BOX_H, inverse ? MAP_BOX_H : MAP_BOX_G, ci, ci,
                     scale, in, out, s, 0);
   }

@@ -64,6 +64,13 @@ struct PassArgs {
   // arithmetic gather table: Btab[e] = (bz[e >> bz_lh][0..d-2], e & (2^bz_lh - 1))
   int bz_arith, bz_lh;
   int bz[64][3];
+  // four-step split of a long last cycle (n = fs_na * nD): the row pass
+  // multiplies (row, element) by exp(-2 pi i lambda_a mu_b / n), lambda_a =
+  // row mod fs_na, after its DFT (forward) or before it (inverse)
+  int fs_na;
+  FastDiv fs_div;
+  const void* fs_lo;  // exp(-2 pi i t / n), t < 2048
+  const void* fs_hi;  // exp(-2 pi i (t << 11) / n)
   int stw_off[4];  // offset of each main stage's twiddles in the stage table
   int stw_n;       // stage table length (complex, even)
   int stw_smem_off;  // its place in shared memory (elements)
@@ -103,10 +110,27 @@ struct PassArgs {
   int alpha[kMaxSub];
 };
 
+// Four-step twiddle exp(-2 pi i lambda_a mu_b / n) of a split last cycle:
+// lambda_a = row mod n_a (the fastest pencil axis), mu_b = element.
+template <typename C>
+__device__ __forceinline__ C fs_twiddle(const PassArgs& a, int row, int e) {
+  const int la = row - a.fs_div.div(row) * a.fs_na;
+  const int t = la * e;  // < n_a n_b = n < 2^31
+  const C* lo = static_cast<const C*>(a.fs_lo);
+  const C* hi = static_cast<const C*>(a.fs_hi);
+  return cmul(__ldg(hi + (t >> 11)), __ldg(lo + (t & 2047)));
+}
+
+template <typename C>
+__device__ __forceinline__ C maybe_conj(C v, int c) {
+  return c ? cconj(v) : v;
+}
+
 // Host-side launcher (fft_kernels.cu).
 int launch_pass(const PassArgs& a, int dtype, cudaStream_t s);
 int launch_twiddles(void* tw, int nD, int dtype, cudaStream_t s);
 int launch_twiddle_gather(void* dst, const void* tw, const int* idx, int n, int dtype, cudaStream_t s);
+int launch_phase_tables(void* tab, int64_t q, int nhi, int dtype, cudaStream_t s);
 int launch_index_probe(const PassArgs& rowp, const PassArgs& colp, int which, int64_t* out,
                        cudaStream_t s);
 

@@ -50,6 +50,34 @@ int launch_twiddle_gather(void* dst, const void* tw, const int* idx, int n, int 
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// Two-level table of exp(-2 pi i t / q): lo[t] for t < 2048, hi[t] = value at
+// t << 11 (exact integer arguments, FP64 sincospi, rounded to the working type).
+template <typename C>
+__global__ void fs_phase_kernel(C* lo, C* hi, long long q, int nhi) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  using Rl = decltype(C::x);
+  double s, c;
+  if (t < 2048) {
+    sincospi(2.0 * double(t % q) / double(q), &s, &c);
+    lo[t] = cmake<C>(Rl(c), Rl(-s));
+  }
+  if (t < nhi) {
+    sincospi(2.0 * double(((long long)t << 11) % q) / double(q), &s, &c);
+    hi[t] = cmake<C>(Rl(c), Rl(-s));
+  }
+}
+
+int launch_phase_tables(void* tab, int64_t q, int nhi, int dtype, cudaStream_t s) {
+  const int n = nhi > 2048 ? nhi : 2048;
+  const int blk = 256, grd = (n + blk - 1) / blk;
+  if (dtype == 0)
+    fs_phase_kernel<float2><<<grd, blk, 0, s>>>(static_cast<float2*>(tab), static_cast<float2*>(tab) + 2048, q, nhi);
+  else
+    fs_phase_kernel<double2><<<grd, blk, 0, s>>>(static_cast<double2*>(tab), static_cast<double2*>(tab) + 2048, q,
+                                                 nhi);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 // Index probe: for every Smith coordinate vector (row-major, flattened as
 // row * nD + element), the box slot the transform kernels read (input map,
 // which = 0) or write (output map, which = 1), evaluated with the same
@@ -64,7 +92,16 @@ __global__ void index_probe_kernel(PassArgs a, const int* __restrict__ PI, int w
     slot = box_sum_slot(a.boxH, a.Atab + row * a.ts, a.Btab + e * a.ts);
   else
     slot = box_sum_slot(a.boxG, a.Ctab + row * a.ts, a.Etab + PI[e] * a.ts);
-  out[w] = slot;
+  // Smith coordinates of (row, e), flattened row-major over the cycles: with a
+  // split last cycle lambda_D = lambda_a + n_a lambda_b (input) and
+  // mu_D = mu_b + n_b mu_a (output), lambda_a / mu_a the fastest row index.
+  int64_t smith = w;
+  if (a.fs_na > 1) {
+    const int ra = row % a.fs_na, rest = row / a.fs_na;
+    const int64_t n = int64_t(a.fs_na) * a.nD;
+    smith = rest * n + (which == 0 ? ra + int64_t(a.fs_na) * e : e + int64_t(a.nD) * ra);
+  }
+  out[smith] = slot;
 }
 
 int launch_index_probe(const PassArgs& rowp, const PassArgs& colp, int which, int64_t* out,

@@ -116,12 +116,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_tma_kernel(PassArgs a) {
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = cconj(v[k]);
   }
+  if (a.fs_na > 1 && a.load_mode == MAP_WS) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = cmul(v[k], fs_twiddle<C>(a, row, p + P * k));
+  }
   cp_async_wait_all();
   __syncthreads();  // staging reads done: the exchange may overwrite it
   fast_pencil_dft<C, R, false>(v, sm, stw, a, p, 0, 1, L);
   // ---- write the row back through the staging buffer
   using Rl = decltype(C::x);
   if (a.store_mode == MAP_WS) {
+    if (a.fs_na > 1) {
+#pragma unroll
+      for (int k = 0; k < R; ++k) v[k] = cmul(v[k], fs_twiddle<C>(a, row, p + P * k));
+    }
 #pragma unroll
     for (int k = 0; k < R; ++k) sm[col_pos(a, p + P * k)] = v[k];
   } else {

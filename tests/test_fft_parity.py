@@ -33,7 +33,9 @@ SMALL = [
     [[2, 1], [1, 1]],                       # unimodular, m = 1
     [[9, 0, 3], [0, 12, 2], [0, 0, 10]],    # fast axis is not a maximal generator
     [[64, 0], [0, 96]],                     # (32, 192): radix 3 with powers of two
-    [[2048, 16], [0, 2048]],                # Table 1 shape, cycles (16, 262144) -> too long
+    [[4, 1], [0, 8192]],                    # one cycle of 32768: split four-step (2 x 16384)
+    [[17, 0], [0, 2048]],                   # one cycle of 34816 = 17 * 2^11: split, mixed radix
+    [[2, 1, 0], [0, 2, 1], [0, 0, 8192]],   # one cycle of 32768 in d = 3
 ]
 
 
@@ -181,3 +183,29 @@ def test_streams_and_repeat_calls_are_deterministic():
         b = plan.forward(c)
     s.synchronize()
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("i", [1, 2, 16, 1024, 0])
+def test_table1_shapes_sampled(i):
+    """The pattern family of Table 1 (Section 6.1): M = [[2048, i], [0, 2048]],
+    m = 2^22, cycles (i, 2^22 / i); cycles longer than one row tile are split."""
+    M = [[2048, i], [0, 2048]]
+    m = 1 << 22
+    plan = pf.PatternFFT(M, 2)
+    c = SI.complex_normal(2, m, 20 + i)
+    y = plan.forward(_gpu(c)).cpu().numpy()
+    slots = SI.sample_slots(m, 512, seed=i)
+    assert rel_l2(y[1:2, slots], oracle.pattern_fft(M, c[1:2], out_slots=slots)) <= 1e-5
+    back = plan.inverse(_gpu(y)).cpu().numpy()
+    assert rel_l2(back, c) <= 1e-5
+    assert np.allclose(np.linalg.norm(y, axis=1), np.linalg.norm(c, axis=1), rtol=1e-5)
+
+
+def test_long_cycle_fp64_full():
+    """A cycle longer than the complex128 row tile (8192), full oracle."""
+    M = [[4, 1], [0, 4096]]  # one cycle of 16384
+    plan = pf.PatternFFT(M, 1, torch.complex128)
+    c = SI.complex_normal(1, plan.m, 5, np.complex128)
+    y = plan.forward(_gpu(c)).cpu().numpy()
+    assert rel_l2(y, oracle.pattern_fft(M, c)) <= 1e-12
+    assert rel_l2(plan.inverse(_gpu(y)).cpu().numpy(), c) <= 1e-12
