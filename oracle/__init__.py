@@ -35,8 +35,9 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-DIRICHLET = 0
-DLVP = 1
+DIRICHLET = 0        # periodised Dirichlet symbol (equals the case formula where it is valid)
+DLVP = 1             # de la Vallee Poussin reading, blend width eta
+DIRICHLET_CASE = 2   # the case formula of Section 6.2 read literally (pins only)
 
 
 def build(force: bool = False) -> str:

@@ -26,14 +26,23 @@
  *     c[h] = sqrt(2) (A(h) d1[g] + B(h) d2[g]) / S,  S = |A(h0)|^2 + |A(h1)|^2,
  *   and the adjoint (conjugate transpose) is c[h] = 2^{-1/2} (A(h) d1 + B(h) d2).
  *
- * Scaling symbols:
- *   DIRICHLET (Section 6.2): with k the representative of h in M^T[-1/2,1/2)^d,
- *     A(h) = 2^{(1 + r_M(k) - r_N(k))/2} if N^{-T} k in [-1/2,1/2]^d, else 0,
- *     r_X(k) = number of coordinates of X^{-T} k equal to +-1/2.
+ * Scaling symbols, both as periodisations over the lattice J^T Z^d,
+ *     w_B(t) = sum_{n in J^T Z^d} prod_j B(t_j + n_j),   t = N^{-T} h:
+ *   DIRICHLET (Section 6.2): A(h) = sqrt(|det J| w(t)) with B the indicator of
+ *     [-1/2, 1/2] taking 1/2 on the boundary, evaluated exactly in integers.
+ *     Section 6.2 defines the symbol through c_k(phi_N) = A(h) c_k(phi_M),
+ *     which presumes phi_N in V_M, i.e. [-1/2,1/2]^d inside J^T[-1/2,1/2]^d
+ *     (true for the paper's dilations).  Where that holds, the periodised form
+ *     equals the paper's case formula (kept below as DIRICHLET_CASE and
+ *     pinned against it):  with k the representative of h in M^T[-1/2,1/2)^d,
+ *       A(h) = 2^{(1 + r_M(k) - r_N(k))/2} if N^{-T} k in [-1/2,1/2]^d, else 0,
+ *       r_X(k) = number of coordinates of X^{-T} k equal to +-1/2.
+ *     For dilations without the containment the case formula breaks perfect
+ *     reconstruction; the periodised form keeps it for every J.
  *   DLVP (not defined in the paper; the reading used by this project):
- *     A(h) = sqrt|det J| * w(N^{-T} h),  w(t) = sum_{n in J^T Z^d} prod_j B(t_j + n_j),
- *     B(s) = clamp(((1+eta)/2 - |s|)/eta, 0, 1).   PARITY UNPINNED beyond perfect
- *     reconstruction, the partition of unity on fibres and the eta -> 0 limit.
+ *     A(h) = sqrt|det J| * w(t),  B(s) = clamp(((1+eta)/2 - |s|)/eta, 0, 1).
+ *     PARITY UNPINNED beyond perfect reconstruction, the partition of unity on
+ *     fibres and the eta -> 0 limit.
  */
 #include <math.h>
 #include <stdint.h>
@@ -163,7 +172,7 @@ static int64_t slot_of(int d, const int64_t* H, const int64_t* y) {
   return s;
 }
 
-enum { PO_DIRICHLET = 0, PO_DLVP = 1 };
+enum { PO_DIRICHLET = 0, PO_DLVP = 1, PO_DIRICHLET_CASE = 2 };
 
 typedef struct {
   int d;
@@ -196,7 +205,7 @@ static double scaling_symbol(const symctx* c, const int64_t* h) {
     for (int i = 0; i < d; ++i) s += (i128)c->J[i * d + j] * u[i];
     v[j] = (int64_t)s;
   }
-  if (c->symbol == PO_DIRICHLET) {
+  if (c->symbol == PO_DIRICHLET_CASE) {
     int rM = 0, rN = 0;
     for (int j = 0; j < d; ++j) {
       if (2 * llabs(v[j]) > q) return 0.0;
@@ -205,18 +214,26 @@ static double scaling_symbol(const symctx* c, const int64_t* h) {
     }
     return pow(2.0, 0.5 * (1 + rM - rN));
   }
-  /* DLVP: periodised trapezoid over the lattice J^T Z^d */
+  /* periodised weight: for each coordinate the shifts n with B(t_j + n) > 0,
+   * t_j = v_j / q; Dirichlet weights decided on exact integer numerators */
   const double eta = c->eta;
-  double wts[8][5];
-  int64_t nval[8][5];
+  double wts[8][6];
+  int64_t nval[8][6];
   int nc[8];
   for (int j = 0; j < d; ++j) {
     nc[j] = 0;
-    for (int64_t n = -2; n <= 2; ++n) {
-      double s = ((double)v[j] + (double)n * (double)q) / (double)q;
-      double b = ((1.0 + eta) / 2.0 - fabs(s)) / eta;
+    const int64_t n0 = floordiv128(-(i128)v[j], q);
+    for (int64_t n = n0 - 2; n <= n0 + 3; ++n) {
+      const i128 a = (i128)v[j] + (i128)n * q; /* numerator of t_j + n */
+      const i128 aa = a < 0 ? -a : a;
+      double b;
+      if (c->symbol == PO_DIRICHLET) {
+        b = (2 * aa < q) ? 1.0 : (2 * aa == q) ? 0.5 : 0.0;
+      } else {
+        b = ((1.0 + eta) / 2.0 - (double)aa / (double)q) / eta;
+        if (b > 1.0) b = 1.0;
+      }
       if (b <= 0.0) continue;
-      if (b > 1.0) b = 1.0;
       wts[j][nc[j]] = b;
       nval[j][nc[j]] = n;
       ++nc[j];
@@ -242,6 +259,7 @@ static double scaling_symbol(const symctx* c, const int64_t* h) {
     while (j >= 0 && ++idx[j] == nc[j]) idx[j--] = 0;
     if (j < 0) break;
   }
+  if (c->symbol == PO_DIRICHLET) return sqrt((double)aJ * w);
   return sqrt((double)aJ) * w;
 }
 
@@ -270,6 +288,7 @@ int po_wavelet_level(int d, const int64_t* HM, const int64_t* HN, const int64_t*
                      int64_t batch, int mode, double* chat, double* d1, double* d2,
                      int nthreads) {
   if (d < 1 || d > 8 || llabs(detJ) != 2) return -1;
+  if (symbol < PO_DIRICHLET || symbol > PO_DIRICHLET_CASE) return -1;
   if (symbol == PO_DLVP && !(eta > 0.0 && eta < 1.0)) return -1;
   int64_t mM = 1, mN = 1, ext[8];
   for (int r = 0; r < d; ++r) {

@@ -333,6 +333,61 @@ def test_dlvp_partition_of_unity_and_dirichlet_limit(M, J):
     assert np.allclose(a0[clean], D0[clean], atol=1e-6) and np.allclose(a1[clean], D1[clean], atol=1e-6)
 
 
+def _containment(J):
+    """[-1/2,1/2]^d inside J^T[-1/2,1/2]^d: every row of J^{-T} has l1 norm <= 1."""
+    JiT = L.inverse(L.transpose(J))
+    return all(sum(abs(x) for x in row) <= 1 for row in JiT)
+
+
+def _fibres(M, J):
+    N = oracle.exact_N(M, J)
+    HN, HM = L.hnf(L.transpose(N)), L.hnf(L.transpose(M))
+    NTl1 = L.matvec(L.transpose(N), oracle.nonzero_class_JT(J))
+    h0 = [L.box_reduce(HM, g) for g in L.box_points(HN)]
+    h1 = [L.box_reduce(HM, [a + b for a, b in zip(g, NTl1)]) for g in L.box_points(HN)]
+    return np.array(h0), np.array(h1)
+
+
+# Dilations of determinant 2 without the containment (parity dilations of the
+# uneven mix, J = I + e_r w^T): the paper's case formula is not a valid symbol there.
+NO_CONTAINMENT = [([[3, 1], [1, 3]], [[1, 0], [-1, 2]]),
+                  ([[10, 1, 7], [0, 9, 1], [0, 0, 32]], [[1, 0, 0], [-1, 2, 0], [0, 0, 1]]),
+                  ([[6, 1, 1], [0, 5, 1], [0, 0, 4]], [[1, 0, 0], [0, 1, 0], [-1, -1, 2]])]
+
+
+@pytest.mark.parametrize("M,J", CASES + [([[6, 2, 0], [0, 6, 2], [0, 0, 4]], [[2, 0, 0], [0, 1, 0], [0, 0, 1]]),
+                                         ([[5, 1, 2], [0, 6, 2], [0, 0, 4]], [[1, 0, 0], [0, 2, 0], [0, 0, 1]])])
+def test_periodised_dirichlet_equals_case_formula(M, J):
+    """Where phi_N lies in V_M ([-1/2,1/2]^d inside J^T[-1/2,1/2]^d, true for
+    the dilations of Section 6.2), the periodised Dirichlet symbol is the
+    paper's case formula on every class of G(M^T)."""
+    assert _containment(J)
+    hs = np.array(list(L.box_points(L.hnf(L.transpose(M)))))
+    a = oracle.scaling_symbol(M, J, hs, oracle.DIRICHLET)
+    b = oracle.scaling_symbol(M, J, hs, oracle.DIRICHLET_CASE)
+    assert np.allclose(a, b, atol=1e-15)
+
+
+@pytest.mark.parametrize("M,J", NO_CONTAINMENT)
+def test_case_formula_fails_without_containment(M, J):
+    """Without the containment the case formula read literally breaks perfect
+    reconstruction (|A(h0)|^2 + |A(h1)|^2 != 2 on some fibre), which is why the
+    oracle uses the periodised form: it sums to 2 on every fibre and gives an
+    orthogonal, norm-preserving split."""
+    assert not _containment(J)
+    h0, h1 = _fibres(M, J)
+    c0 = oracle.scaling_symbol(M, J, h0, oracle.DIRICHLET_CASE)
+    c1 = oracle.scaling_symbol(M, J, h1, oracle.DIRICHLET_CASE)
+    assert not np.allclose(c0 ** 2 + c1 ** 2, 2.0)
+    a0 = oracle.scaling_symbol(M, J, h0, oracle.DIRICHLET)
+    a1 = oracle.scaling_symbol(M, J, h1, oracle.DIRICHLET)
+    assert np.allclose(a0 ** 2 + a1 ** 2, 2.0, atol=1e-14)
+    c, d1, d2, back = _split_roundtrip(M, J, oracle.DIRICHLET, 0.0)
+    assert np.allclose(back, c, atol=1e-12)
+    assert np.allclose(np.linalg.norm(d1, axis=1) ** 2 + np.linalg.norm(d2, axis=1) ** 2,
+                       np.linalg.norm(c, axis=1) ** 2, rtol=1e-13)
+
+
 @pytest.mark.parametrize("symbol", [oracle.DIRICHLET, oracle.DLVP])
 def test_twelve_level_cascade_reconstructs(symbol):
     M0 = [[64, 64], [-64, 64]]  # same shape family as the measured workload, det 2^13
