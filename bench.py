@@ -235,6 +235,47 @@ def bench_wavelet(pf, torch, peaks_hbm, steps=20, warmup=3):
     return out
 
 
+def bench_mix(pf, torch, peaks_hbm, steps=10, warmup=3):
+    """Uneven serving-style mix: 4096 seeded patterns (d in {2, 3}, upper
+    triangular, diagonals in [16, 512], det <= 2^20 and even), forward
+    transform + one Dirichlet split level per pattern (dilation from the
+    pattern's parity), replayed as one CUDA graph with the autotuned schedule.
+    Inputs: seeded complex normal values drawn on the device."""
+    w = SI.WORKLOADS["uneven_mix"]
+    Ms = SI.uneven_mix(w["n_patterns"], seed=w["seed"], even_det=w["even_det"])
+    Js = [SI.parity_dilation(M) for M in Ms]
+    t0 = time.perf_counter()
+    B = pf.PatternBatch(Ms, Js, pf.PWT_DIRICHLET, flags=pf.PFFT_BATCH_AUTOTUNE)
+    t_plan = time.perf_counter() - t0
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w["seed"])
+    x = torch.randn(B.total, dtype=torch.complex64, device="cuda", generator=gen) * math.sqrt(2.0)
+    chat = torch.empty_like(x)
+    sc = torch.empty(B.total // 2, dtype=torch.complex64, device="cuda")
+    wv = torch.empty_like(sc)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "uneven mix: 4096 patterns, forward FFT + one split level each", "patterns": B.n,
+           "points": int(B.total), "plan_s": t_plan, "schedule": dict(zip(("row_budget", "col_budget", "order"),
+                                                                           B.schedule()))}
+    for split, name in ((True, "fft_split"), (False, "fft_only")):
+        for _ in range(warmup):
+            B.forward(x, chat, sc, wv, split=split)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            B.forward(x, chat, sc, wv, split=split)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        alg = (32 if split else 16) * B.total  # compulsory bytes: FFT 8 + 8, split 8 + 4 + 4 per point
+        out[name] = {"value": B.total / (ms * 1e-3), "unit": "points/s", "ms": ms,
+                     "compulsory_gbs": alg / (ms * 1e-3) / 1e9, "compulsory_frac": alg / (ms * 1e-3) / 1e9 / peaks_hbm}
+    B.close()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -304,12 +345,14 @@ def run_native(args):
     value = points / (ms_max * 1e-3)
 
     wavelet = None if args.no_wavelet else bench_wavelet(pf, torch, peaks_hbm=float(measured_peaks()[0]["hbm_gbs"]))
+    mix = None if args.no_mix else bench_mix(pf, torch, peaks_hbm=float(measured_peaks()[0]["hbm_gbs"]))
     if args.no_e2e:
         e2e_value, e2e_ms = None, None
         plan.close()
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "points/s", "ms_per_step": ms_max,
-                              "kernels": prof, "wavelet": wavelet, "note": "profiling run (no e2e)"}), flush=True)
+                              "kernels": prof, "wavelet": wavelet, "uneven_mix": mix,
+                              "note": "profiling run (no e2e)"}), flush=True)
         return 0
     # end to end through the public API with host buffers (pinned), per step:
     # H2D of the input, forward + inverse, D2H of the result
@@ -366,6 +409,7 @@ def run_native(args):
             "kernels": kernels,
             "cpu_baseline": cpu,
             "wavelet": wavelet,
+            "uneven_mix": mix,
             "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": int(x.numel() * 8),
                     "d2h_bytes_per_step": int(z.numel() * 8)},
             "gpu_launches": 4 * args.steps,
@@ -389,6 +433,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--no-wavelet", action="store_true", help="skip the wavelet cascade measurement")
+    ap.add_argument("--no-mix", action="store_true", help="skip the uneven pattern-mix measurement")
     ap.add_argument("--batch", type=int, default=0, help="override the workload batch (profiling runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:

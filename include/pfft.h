@@ -41,12 +41,14 @@
  *  the plan constructors return PFFT_ERR_CUDA.
  *
  *  Limits.  1 <= d <= 4, |M_ij| < 2^24, 1 <= |det M| < 2^31.  The transform
- *  kernels handle at most three non-trivial Smith cycles; the longest cycle
- *  (the last elementary divisor eps_d) must fit one shared-memory tile
- *  (eps_d <= 16384 for PFFT_C64, <= 8192 for PFFT_C128), and so must the
- *  product of the other cycles.  Cycle lengths may contain the prime factors
- *  2, 3, 5, 7, 11, 13, 17, 19, 23, 29 and 31.  Anything else is rejected with
- *  PFFT_ERR_UNSUPPORTED at plan time.
+ *  kernels handle at most three non-trivial Smith cycles.  With the tile
+ *  size S = 16384 (PFFT_C64) or 8192 (PFFT_C128): the product P of all
+ *  cycles but the last must be <= S; the last cycle n either fits (n <= S)
+ *  or splits as n = n_a n_b with n_b <= S and P n_a <= S (four-step split
+ *  inside the two passes).  Cycle lengths may contain any prime factor up to
+ *  1021 (primes from 11 up are evaluated as direct sums: O(p) work per point
+ *  for a factor p).  Anything else is rejected with PFFT_ERR_UNSUPPORTED at
+ *  plan time.
  */
 #ifndef PFFT_H
 #define PFFT_H
@@ -59,6 +61,7 @@ extern "C" {
 
 typedef struct pfft_plan_s* pfft_plan;
 typedef struct pwt_plan_s* pwt_plan;
+typedef struct pfft_batch_s* pfft_batch;
 
 typedef enum {
   PFFT_OK = 0,
@@ -203,6 +206,59 @@ pfft_status pwt_adjoint(pwt_plan p, const void* scaling, const void* const* wave
                         void* stream);
 
 pfft_status pwt_plan_destroy(pwt_plan p);
+
+/* ---------------------------------------------------------------------------
+ * Batches of many patterns of uneven size (serving-style mixes).
+ *
+ * One object holds n patterns M_0 .. M_{n-1} (each with its own d_i) and
+ * optionally one dilation J_i per pattern (|det J_i| = 2, J_i^{-1} M_i
+ * integral).  pfft_batch_forward computes, for every pattern, the transform
+ * of pfft_forward and, when dilations were given, one split level of
+ * pwt_decompose with the batch's symbol (Section 5.3, step 4).  All patterns
+ * run together: three grouped launches (the row pass of every pattern, the
+ * column pass, the split), each CTA finding its pattern in a device table,
+ * with patterns grouped by shared-memory footprint into concurrent launches,
+ * replayed as one CUDA graph.
+ *
+ * Data: the signals are concatenated, pattern i occupying elements
+ * [off_i, off_i + m_i) of `in` and `c_hat`, off_i = m_0 + ... + m_{i-1},
+ * m_i = |det M_i|, each in the box layout of its own plan.  The split parts of
+ * pattern i occupy [off_i / 2, off_i / 2 + m_i / 2) of `scaling` and of
+ * `wavelet` (every m_i is even when dilations are given).  One signal per
+ * pattern (batch 1).
+ * ------------------------------------------------------------------------- */
+enum {
+  PFFT_BATCH_NO_GRAPH = 1u, /* queue the grouped launches directly instead of replaying a graph */
+  PFFT_BATCH_AUTOTUNE = 2u  /* time candidate tile schedules at creation and keep the fastest */
+};
+
+/* n >= 1 patterns; d: host array of n dimensions (1..4); M: host array, the
+ * d_i x d_i row-major matrices one after the other; J: NULL (transforms
+ * only) or dilations in the same layout; symbol / eta as for
+ * pwt_plan_create (ignored when J is NULL); flags: PFFT_BATCH_* bits.
+ * Every pattern is subject to the limits of pfft_plan_create; the first
+ * failing pattern's status is returned and nothing is kept.  Autotuning runs
+ * the batch on scratch buffers it allocates and frees, synchronising the
+ * device. */
+pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, const int64_t* M, const int64_t* J,
+                              int symbol, double eta, int dtype, unsigned flags);
+
+/* m: host array of n (|det M_i|) or NULL; total: sum of m_i or NULL. */
+pfft_status pfft_batch_info(pfft_batch b, int64_t* m, int64_t* total);
+
+/* The chosen schedule: element budgets of the row- and column-pass tiles and
+ * the launch order (1: largest work first, 0: pattern order).  NULLs allowed. */
+pfft_status pfft_batch_schedule(pfft_batch b, int* row_budget, int* col_budget, int* order);
+
+/* in -> c_hat for every pattern; if the batch has dilations and scaling and
+ * wavelet are non-NULL, also c_hat -> (scaling, wavelet).  Device pointers,
+ * layout above.  The graph is built on the first call and rebuilt when any
+ * of the four pointers changes; a batch may be used from one stream at a
+ * time (its workspace is shared). */
+pfft_status pfft_batch_forward(pfft_batch b, const void* in, void* c_hat, void* scaling, void* wavelet,
+                               void* stream);
+
+pfft_status pfft_batch_destroy(pfft_batch b);
 
 /* The same decomposition as pwt_decompose for PFFT_C64 data, but without a
  * plan and without allocating any device memory (the paper has no

@@ -20,15 +20,19 @@ import numpy as np
 import torch
 
 from . import _capi
-from ._capi import (PFFT_C64, PFFT_C128, PFFT_MAP_INPUT_BOX, PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_BOX,
-                    PFFT_MAP_OUTPUT_SNF, PWT_DIRICHLET, PWT_DLVP, PfftError, pfft_device_index_map,
+from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_C64, PFFT_C128, PFFT_MAP_INPUT_BOX,
+                    PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_OUTPUT_SNF, PWT_DIRICHLET, PWT_DLVP,
+                    PfftError, pfft_batch_create, pfft_batch_destroy, pfft_batch_forward, pfft_batch_info,
+                    pfft_batch_schedule, pfft_device_index_map,
                     pfft_forward, pfft_hermite_normal_form, pfft_index_map, pfft_inverse, pfft_plan_create,
                     pfft_last_device_status, pfft_plan_destroy, pfft_plan_info, pfft_profile_enable, pfft_profile_read,
                     pfft_smith_normal_form, pwt_adjoint, pwt_decompose, pwt_plan_create, pwt_plan_destroy,
                     pwt_plan_info, pwt_reconstruct)
 
 __all__ = [
-    "PatternFFT", "WaveletSplit", "pattern_fft", "pattern_ifft", "wavelet_decompose",
+    "PatternFFT", "WaveletSplit", "PatternBatch", "pattern_fft", "pattern_ifft", "wavelet_decompose",
+    "PFFT_BATCH_NO_GRAPH", "PFFT_BATCH_AUTOTUNE", "pfft_batch_create", "pfft_batch_info",
+    "pfft_batch_schedule", "pfft_batch_forward", "pfft_batch_destroy",
     "PfftError", "PFFT_C64", "PFFT_C128", "PWT_DIRICHLET", "PWT_DLVP",
     "PFFT_MAP_INPUT_BOX", "PFFT_MAP_OUTPUT_BOX", "PFFT_MAP_INPUT_SNF", "PFFT_MAP_OUTPUT_SNF",
     "pfft_plan_create", "pfft_plan_info", "pfft_index_map", "pfft_device_index_map", "pfft_forward",
@@ -205,6 +209,58 @@ class WaveletSplit:
     def close(self):
         if getattr(self, "_h", None):
             pwt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PatternBatch:
+    """Many patterns of uneven size, transformed (and split one level) together
+    (wraps pfft_batch).  Signals are concatenated: pattern i owns elements
+    ``offsets[i] : offsets[i] + m[i]`` of the input and of ``c_hat``, and
+    ``offsets[i] // 2 : (offsets[i] + m[i]) // 2`` of the split parts."""
+
+    def __init__(self, Ms, Js=None, symbol: int = PWT_DIRICHLET, eta: float = 0.125, dtype=torch.complex64,
+                 flags: int = 0):
+        self.n = len(Ms)
+        self.dtype = dtype
+        self.has_split = Js is not None
+        self._h = pfft_batch_create(Ms, Js, symbol, eta, _dtype_code(dtype), flags)
+        self.m, self.total = pfft_batch_info(self._h, self.n)
+        self.offsets = np.concatenate([[0], np.cumsum(self.m)[:-1]]).astype(np.int64)
+
+    def schedule(self):
+        """(row tile budget, column tile budget, order) chosen at creation."""
+        return pfft_batch_schedule(self._h)
+
+    def forward(self, x: torch.Tensor, c_hat=None, scaling=None, wavelet=None, split: bool = True, stream=None):
+        """Returns c_hat, or (c_hat, scaling, wavelet) when the batch has dilations and ``split``."""
+        _check_tensor(x, self.dtype, (self.total,), "input")
+        dev = x.device
+        if c_hat is None:
+            c_hat = torch.empty(self.total, dtype=self.dtype, device=dev)
+        _check_tensor(c_hat, self.dtype, (self.total,), "c_hat")
+        if not (self.has_split and split):
+            pfft_batch_forward(self._h, x.data_ptr(), c_hat.data_ptr(), None, None, _stream(stream))
+            return c_hat
+        half = self.total // 2
+        if scaling is None:
+            scaling = torch.empty(half, dtype=self.dtype, device=dev)
+        if wavelet is None:
+            wavelet = torch.empty(half, dtype=self.dtype, device=dev)
+        _check_tensor(scaling, self.dtype, (half,), "scaling")
+        _check_tensor(wavelet, self.dtype, (half,), "wavelet")
+        pfft_batch_forward(self._h, x.data_ptr(), c_hat.data_ptr(), scaling.data_ptr(), wavelet.data_ptr(),
+                           _stream(stream))
+        return c_hat, scaling, wavelet
+
+    def close(self):
+        if getattr(self, "_h", None):
+            pfft_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

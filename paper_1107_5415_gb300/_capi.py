@@ -22,6 +22,7 @@ _lib = None
 PFFT_C64, PFFT_C128 = 0, 1
 PFFT_MAP_INPUT_BOX, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_SNF = 0, 1, 2, 3
 PWT_DIRICHLET, PWT_DLVP = 0, 1
+PFFT_BATCH_NO_GRAPH, PFFT_BATCH_AUTOTUNE = 1, 2
 
 STATUS = {0: "PFFT_OK", 1: "PFFT_ERR_ARG", 2: "PFFT_ERR_SINGULAR", 3: "PFFT_ERR_OVERFLOW",
           4: "PFFT_ERR_NOT_INTEGRAL", 5: "PFFT_ERR_UNSUPPORTED", 6: "PFFT_ERR_OOM", 7: "PFFT_ERR_CUDA",
@@ -70,6 +71,13 @@ _SIGS = {
     "pwt_decompose_noalloc": (ctypes.c_int, [ctypes.c_int, _i64p, ctypes.c_int, _i64p, ctypes.c_int,
                                              ctypes.c_double, ctypes.c_int64, _vp, _vp, ctypes.POINTER(_vp),
                                              _vp]),
+    "pfft_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i64p,
+                                         _i64p, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_uint]),
+    "pfft_batch_info": (ctypes.c_int, [_vp, _i64p, _i64p]),
+    "pfft_batch_schedule": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]),
+    "pfft_batch_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "pfft_batch_destroy": (ctypes.c_int, [_vp]),
 }
 
 
@@ -245,3 +253,51 @@ def pwt_decompose_noalloc(M, Js, symbol: int, eta: float, batch: int, c_hat_ptr:
     arr = _ptr_array(wavelet_ptrs)
     _check(lib().pwt_decompose_noalloc(d, p, levels, jp, int(symbol), float(eta), int(batch), c_hat_ptr,
                                        scaling_ptr, arr, stream), "pwt_decompose_noalloc")
+
+
+# ------------------------------------------------------------ pattern batches
+def pfft_batch_create(Ms, Js=None, symbol: int = PWT_DIRICHLET, eta: float = 0.125, dtype: int = PFFT_C64,
+                      flags: int = 0):
+    """Ms: sequence of square integer matrices (any mix of d); Js: None or one
+    dilation per pattern, each of its pattern's d."""
+    ds = [int(np.asarray(M).shape[0]) for M in Ms]
+    for M, d in zip(Ms, ds):
+        if np.asarray(M).shape != (d, d):
+            raise ValueError("every M must be square")
+    d_arr = (ctypes.c_int * len(ds))(*ds)
+    ma, mp = _i64(np.concatenate([np.asarray(M, dtype=np.int64).reshape(-1) for M in Ms]))
+    jp = None
+    if Js is not None:
+        if len(Js) != len(Ms):
+            raise ValueError("one dilation per pattern is required")
+        for J, d in zip(Js, ds):
+            if np.asarray(J).shape != (d, d):
+                raise ValueError("each J must have the shape of its M")
+        ja, jp = _i64(np.concatenate([np.asarray(J, dtype=np.int64).reshape(-1) for J in Js]))
+    h = _vp()
+    _check(lib().pfft_batch_create(ctypes.byref(h), len(ds), d_arr, mp, jp, int(symbol), float(eta), int(dtype),
+                                   int(flags)), "pfft_batch_create")
+    return h.value
+
+
+def pfft_batch_info(batch, n: int):
+    m, mp = _i64(np.zeros(n))
+    total = ctypes.c_int64()
+    _check(lib().pfft_batch_info(batch, mp, ctypes.byref(total)), "pfft_batch_info")
+    return m, total.value
+
+
+def pfft_batch_schedule(batch):
+    r, c, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().pfft_batch_schedule(batch, ctypes.byref(r), ctypes.byref(c), ctypes.byref(o)),
+           "pfft_batch_schedule")
+    return r.value, c.value, o.value
+
+
+def pfft_batch_forward(batch, in_ptr: int, c_hat_ptr: int, scaling_ptr, wavelet_ptr, stream: int):
+    _check(lib().pfft_batch_forward(batch, in_ptr, c_hat_ptr, scaling_ptr, wavelet_ptr, stream),
+           "pfft_batch_forward")
+
+
+def pfft_batch_destroy(batch):
+    _check(lib().pfft_batch_destroy(batch), "pfft_batch_destroy")

@@ -1,0 +1,474 @@
+// Batches of many patterns of uneven size: host planning, the schedule of
+// grouped launches, CUDA-graph replay and the schedule autotuner.
+//
+// Every pattern gets an ordinary transform plan (exact SNF and tables, the
+// same device code as pfft_forward) restricted to the generic shared-memory
+// kernels, whose tables are sub-allocated from one arena.  A schedule turns
+// the plans into grouped launches: for each pass, the patterns are grouped by
+// the shared-memory footprint of their tile into at most kMaxBuckets
+// launches (so that small tiles are not held to the occupancy of the largest
+// one), those launches run concurrently on forked streams, and inside a
+// launch the CTAs of the costliest tiles come first.  The split level of every
+// pattern is one more grouped launch.  The autotuner times candidate tile
+// budgets and orders on the real batch and keeps the fastest.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pfft.h"
+#include "batch.hpp"
+#include "plan_internal.hpp"
+
+using namespace pfft;
+
+namespace {
+constexpr int kMaxBuckets = 5;
+// upper ends of the shared-memory classes of a grouped pass launch (bytes)
+constexpr int kSmemClass[kMaxBuckets] = {24 * 1024, 48 * 1024, 72 * 1024, 112 * 1024, kGroupedMaxDynSmem};
+
+struct Bucket {
+  int cols = 0, n = 0, nctas = 0, threads = 0, smem = 0;
+  size_t items_off = 0, cta0_off = 0;  // byte offsets into the schedule buffer
+};
+}  // namespace
+
+struct pfft_batch_s {
+  int n = 0, dtype = 0;
+  unsigned flags = 0;
+  Arena arena;  // declared first: destroyed after the plans are released
+  std::vector<pfft_plan_s*> plans;
+  std::vector<int64_t> m, off;
+  int64_t total = 0;
+  bool has_split = false;
+  std::vector<SplitItem> sitems;
+  void* ws = nullptr;
+  void* sched = nullptr;  // device: items and first-CTA tables of all launches
+  std::vector<Bucket> rows, cols, splits;
+  int row_budget = 8192, col_budget = 8192, order = 1;
+  std::vector<int> ident;  // patterns with m = 1 (the transform is a copy)
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  cudaGraphExec_t exec = nullptr;
+  const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
+
+  ~pfft_batch_s() {
+    for (auto* P : plans) plan_release(P);
+    if (exec) cudaGraphExecDestroy(exec);
+    for (auto e : events) cudaEventDestroy(e);
+    for (auto s : streams) cudaStreamDestroy(s);
+    if (cap) cudaStreamDestroy(cap);
+    if (sched) cudaFree(sched);
+    if (ws) cudaFree(ws);
+  }
+};
+
+namespace {
+
+size_t ebytes(int dtype) { return dtype == PFFT_C64 ? 8 : 16; }
+
+// Relative cost of one CTA of a pass: its elements times the per-element work
+// of its stages (direct prime stages cost about R / 4 radix-2 butterflies).
+double tile_cost(const PassArgs& a) {
+  double w = 0;
+  for (int i = 0; i < a.nstages; ++i) {
+    const int R = a.st[i].R;
+    w += R >= kMinDirectRadix ? R / 4.0 : std::log2(double(R));
+  }
+  return double(a.T) * a.L * (w + 2.0);
+}
+
+struct Item {
+  PassArgs a;
+  int pattern;
+  double cost;
+};
+
+// Group items into launches by shared-memory class; order each launch.
+void make_buckets(std::vector<Item>& items, int cols, int order, std::vector<Bucket>& out,
+                  std::vector<std::vector<Item>>& groups) {
+  std::vector<std::vector<Item>> g(kMaxBuckets);
+  for (auto& it : items) {
+    int c = 0;
+    while (c + 1 < kMaxBuckets && it.a.smem_bytes > kSmemClass[c]) ++c;
+    g[c].push_back(it);
+  }
+  for (auto& v : g) {
+    if (v.empty()) continue;
+    if (order == 1)
+      std::stable_sort(v.begin(), v.end(), [](const Item& x, const Item& y) { return x.cost > y.cost; });
+    Bucket b;
+    b.cols = cols;
+    b.n = int(v.size());
+    for (auto& it : v) {
+      b.nctas += it.a.groups;
+      b.threads = std::max(b.threads, it.a.nthreads);
+      b.smem = std::max(b.smem, it.a.smem_bytes);
+    }
+    out.push_back(b);
+    groups.push_back(std::move(v));
+  }
+}
+
+pfft_status build_schedule(pfft_batch_s& B) {
+  const size_t eb = ebytes(B.dtype);
+  std::vector<Item> rows, cols;
+  for (int i = 0; i < B.n; ++i) {
+    pfft_plan_s* P = B.plans[i];
+    if (P->D == 0) continue;
+    pfft_status st = plan_retile(*P, B.row_budget, B.col_budget);
+    if (st != PFFT_OK) return st;
+    const double scale = 1.0 / std::sqrt(double(P->m));
+    const uintptr_t boff = uintptr_t(B.off[i]) * eb;
+    PassArgs r = P->rowp;
+    r.batch = 1;
+    r.load_mode = MAP_BOX_H;
+    r.conj_in = r.conj_out = 0;
+    r.in_sel = 0;
+    r.in = reinterpret_cast<const void*>(boff);
+    r.out = reinterpret_cast<void*>(boff);
+    if (P->pen.empty()) {
+      r.store_mode = MAP_BOX_G;
+      r.scale = scale;
+      r.out_sel = 2;
+    } else {
+      r.store_mode = MAP_WS;
+      r.scale = 1.0;
+      r.out_sel = 1;
+    }
+    rows.push_back({r, i, tile_cost(r)});
+    if (!P->pen.empty()) {
+      PassArgs c = P->colp;
+      c.batch = 1;
+      c.load_mode = MAP_WS;
+      c.store_mode = MAP_BOX_G;
+      c.conj_in = c.conj_out = 0;
+      c.scale = scale;
+      c.in_sel = 1;
+      c.out_sel = 2;
+      c.in = reinterpret_cast<const void*>(boff);
+      c.out = reinterpret_cast<void*>(boff);
+      cols.push_back({c, i, tile_cost(c)});
+    }
+  }
+  std::vector<Bucket> rb, cb, sb;
+  std::vector<std::vector<Item>> rg, cg;
+  make_buckets(rows, 0, B.order, rb, rg);
+  make_buckets(cols, 1, B.order, cb, cg);
+  // split launch: one item per pattern, costliest first
+  std::vector<int> sorder;
+  for (int i = 0; i < int(B.sitems.size()); ++i) sorder.push_back(i);
+  if (B.order == 1)
+    std::stable_sort(sorder.begin(), sorder.end(),
+                     [&](int x, int y) { return B.sitems[x].L.mN > B.sitems[y].L.mN; });
+  // lay out the schedule buffer
+  std::vector<char> host;
+  auto put = [&](const void* p, size_t bytes) {
+    const size_t o = (host.size() + 255) & ~size_t(255);
+    host.resize(o + bytes);
+    std::memcpy(host.data() + o, p, bytes);
+    return o;
+  };
+  auto put_group = [&](Bucket& b, const std::vector<Item>& v) {
+    std::vector<PassArgs> a(v.size());
+    std::vector<int> c0(v.size() + 1, 0);
+    for (size_t k = 0; k < v.size(); ++k) {
+      a[k] = v[k].a;
+      c0[k + 1] = c0[k] + v[k].a.groups;
+    }
+    b.items_off = put(a.data(), a.size() * sizeof(PassArgs));
+    b.cta0_off = put(c0.data(), c0.size() * sizeof(int));
+  };
+  for (size_t k = 0; k < rb.size(); ++k) put_group(rb[k], rg[k]);
+  for (size_t k = 0; k < cb.size(); ++k) put_group(cb[k], cg[k]);
+  if (!sorder.empty()) {
+    std::vector<SplitItem> si;
+    std::vector<int> c0(1, 0);
+    for (int i : sorder) {
+      si.push_back(B.sitems[i]);
+      c0.push_back(c0.back() + int((B.sitems[i].L.mN + kSplitThreads - 1) / kSplitThreads));
+    }
+    Bucket b;
+    b.n = int(si.size());
+    b.nctas = c0.back();
+    b.threads = kSplitThreads;
+    b.items_off = put(si.data(), si.size() * sizeof(SplitItem));
+    b.cta0_off = put(c0.data(), c0.size() * sizeof(int));
+    sb.push_back(b);
+  }
+  void* dev = nullptr;
+  if (!host.empty()) {
+    if (int e = device_alloc(&dev, host.size())) return pfft_status(e);
+    if (cudaMemcpy(dev, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(dev);
+      return PFFT_ERR_CUDA;
+    }
+  }
+  if (B.sched) cudaFree(B.sched);
+  B.sched = dev;
+  B.rows = rb;
+  B.cols = cb;
+  B.splits = sb;
+  if (B.exec) {  // the graph refers to the old schedule
+    cudaGraphExecDestroy(B.exec);
+    B.exec = nullptr;
+  }
+  return PFFT_OK;
+}
+
+// Queue the whole batch on stream s (directly, or into a capture of s).
+pfft_status enqueue(pfft_batch_s& B, const void* in, void* chat, void* sc, void* wv, cudaStream_t s) {
+  const size_t eb = ebytes(B.dtype);
+  for (int i : B.ident)
+    if (cudaMemcpyAsync(static_cast<char*>(chat) + B.off[i] * eb, static_cast<const char*>(in) + B.off[i] * eb, eb,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return PFFT_ERR_CUDA;
+  const char* sched = static_cast<const char*>(B.sched);
+  auto phase = [&](const std::vector<Bucket>& bs) -> pfft_status {
+    auto launch = [&](const Bucket& b, cudaStream_t st) {
+      GroupArgs g;
+      g.items = reinterpret_cast<const PassArgs*>(sched + b.items_off);
+      g.cta0 = reinterpret_cast<const int*>(sched + b.cta0_off);
+      g.n = b.n;
+      g.base[0] = in;
+      g.base[1] = B.ws;
+      g.base[2] = chat;
+      return launch_grouped_pass(g, b.cols, B.dtype, b.nctas, b.threads, b.smem, st);
+    };
+    if (bs.empty()) return PFFT_OK;
+    if (bs.size() == 1) return launch(bs[0], s) == 0 ? PFFT_OK : PFFT_ERR_CUDA;
+    if (cudaEventRecord(B.events[0], s) != cudaSuccess) return PFFT_ERR_CUDA;
+    for (size_t k = 0; k < bs.size(); ++k) {
+      if (cudaStreamWaitEvent(B.streams[k], B.events[0], 0) != cudaSuccess) return PFFT_ERR_CUDA;
+      if (launch(bs[k], B.streams[k]) != 0) return PFFT_ERR_CUDA;
+      if (cudaEventRecord(B.events[1 + k], B.streams[k]) != cudaSuccess) return PFFT_ERR_CUDA;
+    }
+    for (size_t k = 0; k < bs.size(); ++k)
+      if (cudaStreamWaitEvent(s, B.events[1 + k], 0) != cudaSuccess) return PFFT_ERR_CUDA;
+    return PFFT_OK;
+  };
+  pfft_status st = phase(B.rows);
+  if (st != PFFT_OK) return st;
+  st = phase(B.cols);
+  if (st != PFFT_OK) return st;
+  if (sc && wv && !B.splits.empty()) {
+    const Bucket& b = B.splits[0];
+    if (launch_grouped_split(reinterpret_cast<const SplitItem*>(sched + b.items_off),
+                             reinterpret_cast<const int*>(sched + b.cta0_off), b.n, b.nctas, chat, sc, wv, B.dtype,
+                             s) != 0)
+      return PFFT_ERR_CUDA;
+  }
+  return PFFT_OK;
+}
+
+pfft_status run_graph(pfft_batch_s& B, const void* in, void* chat, void* sc, void* wv, cudaStream_t s) {
+  const void* key[4] = {in, chat, sc, wv};
+  if (!B.exec || std::memcmp(key, B.key, sizeof(key)) != 0) {
+    if (cudaStreamBeginCapture(B.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PFFT_ERR_CUDA;
+    pfft_status st = enqueue(B, in, chat, sc, wv, B.cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(B.cap, &g);
+    if (st != PFFT_OK || ce != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return st != PFFT_OK ? st : PFFT_ERR_CUDA;
+    }
+    if (B.exec) cudaGraphExecDestroy(B.exec);
+    B.exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&B.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      B.exec = nullptr;
+      return PFFT_ERR_CUDA;
+    }
+    std::memcpy(B.key, key, sizeof(key));
+  }
+  return cudaGraphLaunch(B.exec, s) == cudaSuccess ? PFFT_OK : PFFT_ERR_CUDA;
+}
+
+// Mean time (ms) of `reps` direct runs of the current schedule.
+pfft_status time_schedule(pfft_batch_s& B, const void* in, void* chat, void* sc, void* wv, int reps, float* ms) {
+  cudaStream_t s = B.cap;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return PFFT_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PFFT_ERR_CUDA;
+  }
+  pfft_status st = enqueue(B, in, chat, sc, wv, s);  // warm-up
+  if (st == PFFT_OK) cudaEventRecord(e0, s);
+  for (int r = 0; r < reps && st == PFFT_OK; ++r) st = enqueue(B, in, chat, sc, wv, s);
+  if (st == PFFT_OK) {
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      st = PFFT_ERR_CUDA;
+    *ms /= float(reps);
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+// Coordinate search over the row budget, the column budget and the order.
+pfft_status autotune(pfft_batch_s& B) {
+  const size_t eb = ebytes(B.dtype);
+  void *in = nullptr, *chat = nullptr, *sc = nullptr, *wv = nullptr;
+  pfft_status st = PFFT_OK;
+  auto fail = [&](pfft_status e) {
+    for (void* p : {in, chat, sc, wv})
+      if (p) cudaFree(p);
+    return e;
+  };
+  if (int e = device_alloc(&in, size_t(B.total) * eb)) return fail(pfft_status(e));
+  if (int e = device_alloc(&chat, size_t(B.total) * eb)) return fail(pfft_status(e));
+  if (B.has_split) {
+    if (int e = device_alloc(&sc, size_t(B.total / 2) * eb)) return fail(pfft_status(e));
+    if (int e = device_alloc(&wv, size_t(B.total / 2) * eb)) return fail(pfft_status(e));
+  }
+  if (cudaMemset(in, 0, size_t(B.total) * eb) != cudaSuccess) return fail(PFFT_ERR_CUDA);
+  const int budgets[] = {2048, 4096, 8192, 16384};
+  float best = 1e30f;
+  int br = B.row_budget, bc = B.col_budget, bo = B.order;
+  auto trial = [&](int r, int c, int o) -> pfft_status {
+    B.row_budget = r;
+    B.col_budget = c;
+    B.order = o;
+    pfft_status e = build_schedule(B);
+    if (e != PFFT_OK) return e;
+    float ms = 0;
+    e = time_schedule(B, in, chat, sc, wv, 3, &ms);
+    if (e != PFFT_OK) return e;
+    if (ms < best) {
+      best = ms;
+      br = r;
+      bc = c;
+      bo = o;
+    }
+    return PFFT_OK;
+  };
+  for (int r : budgets)
+    if ((st = trial(r, bc, bo)) != PFFT_OK) return fail(st);
+  for (int c : budgets)
+    if ((st = trial(br, c, bo)) != PFFT_OK) return fail(st);
+  if ((st = trial(br, bc, 1 - bo)) != PFFT_OK) return fail(st);
+  B.row_budget = br;
+  B.col_budget = bc;
+  B.order = bo;
+  st = build_schedule(B);
+  return fail(st);
+}
+
+}  // namespace
+
+extern "C" pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, const int64_t* M, const int64_t* J,
+                                         int symbol, double eta, int dtype, unsigned flags) {
+  if (!out || n < 1 || !d || !M || (dtype != PFFT_C64 && dtype != PFFT_C128) ||
+      (flags & ~unsigned(PFFT_BATCH_NO_GRAPH | PFFT_BATCH_AUTOTUNE)))
+    return PFFT_ERR_ARG;
+  if (J && (symbol != PWT_DIRICHLET && symbol != PWT_DLVP)) return PFFT_ERR_ARG;
+  if (J && symbol == PWT_DLVP && !(eta > 0.0 && eta < 1.0)) return PFFT_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (d[i] < 1 || d[i] > 4) return PFFT_ERR_ARG;
+  pfft_batch_s* B = new (std::nothrow) pfft_batch_s;
+  if (!B) return PFFT_ERR_OOM;
+  B->n = n;
+  B->dtype = dtype;
+  B->flags = flags;
+  B->has_split = J != nullptr;
+  auto fail = [&](pfft_status st) {
+    delete B;
+    return st;
+  };
+  if (prepare_grouped(dtype) != 0) return fail(PFFT_ERR_CUDA);
+  size_t mo = 0;
+  bool need_ws = false;
+  for (int i = 0; i < n; ++i) {
+    pfft_plan_s* P = new (std::nothrow) pfft_plan_s;
+    if (!P) return fail(PFFT_ERR_OOM);
+    B->plans.push_back(P);
+    P->batch = 1;
+    P->dtype = dtype;
+    P->arena = &B->arena;
+    P->generic_only = true;
+    P->own_workspace = false;
+    pfft_status st;
+    try {
+      st = plan_host(*P, d[i], M + mo);
+      if (st == PFFT_OK) st = plan_device(*P);
+    } catch (const LatticeError& e) {
+      st = pfft_status(e.code);
+    }
+    if (st != PFFT_OK) return fail(st);
+    B->m.push_back(P->m);
+    B->off.push_back(B->total);
+    B->total += P->m;
+    if (P->D == 0) B->ident.push_back(i);
+    if (!P->pen.empty()) need_ws = true;
+    if (J) {
+      SplitItem it;
+      std::memset(&it, 0, sizeof(it));
+      st = describe_split_level(d[i], M + mo, J + mo, symbol, eta, &it.L);
+      if (st != PFFT_OK) return fail(st);
+      it.in_off = B->off[i];
+      it.out_off = B->off[i] / 2;
+      B->sitems.push_back(it);
+    }
+    mo += size_t(d[i]) * d[i];
+  }
+  if (B->total >= (int64_t(1) << 40)) return fail(PFFT_ERR_OVERFLOW);
+  if (need_ws)
+    if (int e = device_alloc(&B->ws, size_t(B->total) * ebytes(dtype))) return fail(pfft_status(e));
+  if (cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(PFFT_ERR_CUDA);
+  for (int k = 0; k < kMaxBuckets; ++k) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(PFFT_ERR_CUDA);
+    B->streams.push_back(s);
+  }
+  for (int k = 0; k < kMaxBuckets + 1; ++k) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(PFFT_ERR_CUDA);
+    B->events.push_back(e);
+  }
+  pfft_status st = (flags & PFFT_BATCH_AUTOTUNE) ? autotune(*B) : build_schedule(*B);
+  if (st != PFFT_OK) return fail(st);
+  *out = B;
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pfft_batch_info(pfft_batch b, int64_t* m, int64_t* total) {
+  if (!b) return PFFT_ERR_ARG;
+  if (m)
+    for (int i = 0; i < b->n; ++i) m[i] = b->m[i];
+  if (total) *total = b->total;
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pfft_batch_schedule(pfft_batch b, int* row_budget, int* col_budget, int* order) {
+  if (!b) return PFFT_ERR_ARG;
+  if (row_budget) *row_budget = b->row_budget;
+  if (col_budget) *col_budget = b->col_budget;
+  if (order) *order = b->order;
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pfft_batch_forward(pfft_batch b, const void* in, void* c_hat, void* scaling, void* wavelet,
+                                          void* stream) {
+  if (!b || !in || !c_hat || in == c_hat) return PFFT_ERR_ARG;
+  if ((scaling == nullptr) != (wavelet == nullptr)) return PFFT_ERR_ARG;
+  if (scaling && !b->has_split) return PFFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (b->flags & PFFT_BATCH_NO_GRAPH) return enqueue(*b, in, c_hat, scaling, wavelet, s);
+  return run_graph(*b, in, c_hat, scaling, wavelet, s);
+}
+
+extern "C" pfft_status pfft_batch_destroy(pfft_batch b) {
+  if (!b) return PFFT_ERR_ARG;
+  delete b;
+  return PFFT_OK;
+}

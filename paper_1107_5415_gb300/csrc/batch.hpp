@@ -1,0 +1,41 @@
+// Descriptors of the grouped launches of a pattern batch (batch.cu host side,
+// batch_kernels.cu device side).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fft_plan.hpp"
+#include "wavelet_kernels.cuh"
+
+namespace pfft {
+
+constexpr int kSplitThreads = 256;
+// Dynamic shared memory of a grouped pass CTA: the 227 KB per CTA less room
+// for the static copy of its pass descriptor.
+constexpr int kGroupedMaxDynSmem = 227 * 1024 - 4096;
+
+// One grouped pass launch: items[k] is the descriptor of the k-th pattern of
+// the launch, whose tiles are CTAs cta0[k] .. cta0[k+1]-1.  The in / out
+// fields of an item hold byte offsets into base[in_sel] / base[out_sel].
+struct GroupArgs {
+  const PassArgs* items;
+  const int* cta0;
+  int n;
+  const void* base[3];  // 0: the caller's input, 1: the batch workspace, 2: the caller's output
+};
+
+// One split level of one pattern; offsets in elements into the concatenated
+// c_hat (in_off) and split parts (out_off).
+struct alignas(16) SplitItem {
+  LevelDesc L;
+  long long in_off, out_off;
+};
+
+// Raise the dynamic shared-memory limit of the grouped kernels (once per
+// process; call before any stream capture).
+int prepare_grouped(int dtype);
+int launch_grouped_pass(const GroupArgs& g, int cols, int dtype, int nctas, int threads, int smem,
+                        cudaStream_t s);
+int launch_grouped_split(const SplitItem* items, const int* cta0, int n, int nctas, const void* chat, void* sc,
+                         void* wv, int dtype, cudaStream_t s);
+
+}  // namespace pfft

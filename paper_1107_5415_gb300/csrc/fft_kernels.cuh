@@ -80,9 +80,107 @@ __device__ __forceinline__ void run_stage(C* sm, const PassArgs& a, const StageD
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     if (obase[q] >= 0) {
-      dft<C, R>(v[q], tw, a.nD);
+      dft<C, R>(v[q], tw, a.tw_n);
 #pragma unroll
       for (int r = 0; r < R; ++r) sm[phys(obase[q] + r * ostep)] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+// One stage of a prime radix R >= 11, evaluated directly: with
+// x'_r = x_r exp(-2 pi i r k / (Ns R)) (k = j mod Ns, applied in place first
+// when Ns > 1), output s of butterfly j is sum_r x'_r omega_R^(r s).  Outputs
+// s and R - s share the products (their twiddles are conjugate), so one work
+// item accumulates four real sums for the pair.  Lanes of a warp take
+// consecutive butterflies of the same output pair: the x reads are
+// consecutive and the omega_R reads (a table of R entries after the tile) are
+// broadcasts.  Every read of the stage happens before its first write.
+template <typename C, int NBI, bool COLS>
+__device__ __noinline__ void run_direct_stage(C* sm, const PassArgs& a, const StageDesc& s,
+                                              const C* __restrict__ tw) {
+  using Rl = decltype(C::x);
+  const int R = s.R;
+  const int per_pencil = a.L / R;
+  const int nbfly = a.T * per_pencil;
+  const int npair = (R + 1) / 2;
+  const int nthr = blockDim.x;
+  const int escale = COLS ? a.T : 1;
+  const int step = s.sigma * escale;
+  C* W = sm + a.dir_off;
+  const int wstride = a.tw_n / R;
+  for (int e = threadIdx.x; e < R; e += nthr) W[e] = __ldg(tw + e * wstride);
+  auto locate = [&](int b, int& ebase, int& k, int& j) {
+    int t, rest;
+    if (COLS) {
+      rest = a.divT.div(b);
+      t = b - rest * a.T;
+    } else {
+      t = b / per_pencil;
+      rest = b - t * per_pencil;
+    }
+    const int o = s.div_aR.div(rest);
+    j = rest - o * s.aR;
+    const int hi = s.div_sigma.div(o);
+    const int base = hi * s.a * s.sigma + (o - hi * s.sigma);
+    k = j - s.div_Ns.div(j) * s.Ns;
+    ebase = COLS ? base * a.T + t : t * a.L + base;
+  };
+  if (s.Ns > 1) {  // x_r *= exp(-2 pi i r k / (Ns R)), in place (one owner per element)
+    const int NsR = s.Ns * R;
+    for (int w = threadIdx.x; w < nbfly * R; w += nthr) {
+      const int r = w / nbfly;
+      const int b = w - r * nbfly;
+      int ebase, k, j;
+      locate(b, ebase, k, j);
+      const int idx = int((int64_t(r) * k) % NsR);
+      if (idx) {
+        C* x = sm + phys(ebase + (j + r * s.aR) * step);
+        *x = cmul(*x, __ldg(tw + idx * s.twstep));
+      }
+    }
+  }
+  __syncthreads();
+  C y0[NBI], y1[NBI];
+  int ob[NBI], qs[NBI];
+#pragma unroll
+  for (int u = 0; u < NBI; ++u) {
+    const int w = threadIdx.x + u * nthr;
+    ob[u] = -1;
+    if (w < nbfly * npair) {
+      const int q = w / nbfly;
+      const int b = w - q * nbfly;
+      int ebase, k, j;
+      locate(b, ebase, k, j);
+      const C* x = sm;
+      const int i0 = ebase + j * step;
+      const int istep = s.aR * step;
+      Rl A = 0, B = 0, Cs = 0, Ds = 0;
+      int idx = 0;
+#pragma unroll 4
+      for (int r = 0; r < R; ++r) {
+        const C xv = x[phys(i0 + r * istep)];
+        const C wv = W[idx];
+        A = fma(xv.x, wv.x, A);
+        B = fma(xv.y, wv.y, B);
+        Cs = fma(xv.x, wv.y, Cs);
+        Ds = fma(xv.y, wv.x, Ds);
+        idx += q;
+        if (idx >= R) idx -= R;
+      }
+      y0[u] = cmake<C>(A - B, Cs + Ds);  // output q
+      y1[u] = cmake<C>(A + B, Ds - Cs);  // output R - q
+      ob[u] = ebase + ((j - k) * R + k) * step;
+      qs[u] = q;
+    }
+  }
+  __syncthreads();
+  const int ostep = s.Ns * step;
+#pragma unroll
+  for (int u = 0; u < NBI; ++u) {
+    if (ob[u] >= 0) {
+      sm[phys(ob[u] + qs[u] * ostep)] = y0[u];
+      if (qs[u] > 0) sm[phys(ob[u] + (R - qs[u]) * ostep)] = y1[u];
     }
   }
   __syncthreads();
@@ -97,6 +195,10 @@ __device__ __forceinline__ void run_stage(C* sm, const PassArgs& a, const StageD
 template <typename C, int EPT, bool COLS, bool POW2>
 __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ tw) {
   int i = 0;
+  if constexpr (!POW2) {
+    _Pragma("unroll 1") for (int q = 0; q < a.cnt[kDirectRegion]; ++q, ++i)
+        run_direct_stage<C, kDirectItems<EPT>, COLS>(sm, a, a.st[i], tw);
+  }
 #define PFFT_REGION(RR, IDX)                                                     \
   _Pragma("unroll 1") for (int q = 0; q < a.cnt[IDX]; ++q, ++i)                  \
       run_stage<C, RR, (EPT / RR > 0 ? EPT / RR : 1), COLS>(sm, a, a.st[i], tw);
@@ -108,13 +210,6 @@ __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ t
     PFFT_REGION(3, 4)
     PFFT_REGION(5, 5)
     PFFT_REGION(7, 6)
-    PFFT_REGION(11, 7)
-    PFFT_REGION(13, 8)
-    PFFT_REGION(17, 9)
-    PFFT_REGION(19, 10)
-    PFFT_REGION(23, 11)
-    PFFT_REGION(29, 12)
-    PFFT_REGION(31, 13)
   }
 #undef PFFT_REGION
 }
@@ -124,14 +219,16 @@ __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ t
 // owns at most EPT elements of the tile: all of its global loads are issued
 // before the first shared-memory write (and all shared reads before the
 // first global store), so the loads of a thread are in flight together.
+//
+// The body takes the tile (blockIdx.x of a plain launch) and the signal index
+// (blockIdx.y) as arguments so that the grouped launches of many patterns
+// (batch_kernels.cu) run the same code on a per-CTA copy of the arguments.
 template <typename C, int EPT, bool POW2>
-__global__ void __launch_bounds__(kMaxThreads, 1) row_pass_kernel(PassArgs a) {
-  extern __shared__ unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
+__device__ __forceinline__ void row_pass_body(const PassArgs& a, int tile, int sig, C* sm) {
   const C* __restrict__ tw = static_cast<const C*>(a.tw);
-  const C* __restrict__ in = static_cast<const C*>(a.in) + (int64_t)blockIdx.y * a.m;
-  C* __restrict__ out = static_cast<C*>(a.out) + (int64_t)blockIdx.y * a.m;
-  const int r0 = blockIdx.x * a.T;
+  const C* __restrict__ in = static_cast<const C*>(a.in) + (int64_t)sig * a.m;
+  C* __restrict__ out = static_cast<C*>(a.out) + (int64_t)sig * a.m;
+  const int r0 = tile * a.T;
   const int n = a.T * a.nD;
   const int d = a.d;
   const int nthr = blockDim.x;
@@ -232,25 +329,26 @@ __device__ __forceinline__ int shear_index(const PassArgs& a, int j, const int* 
 // layout [i][t].  The DFT runs over the (D-1) cycles inside the pencil.
 // Loads and stores are batched per thread as in the row pass.
 template <typename C, int EPT, bool POW2>
-__global__ void __launch_bounds__(kMaxThreads, 1) col_pass_kernel(PassArgs a) {
-  extern __shared__ unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
+__device__ __forceinline__ void col_pass_body(const PassArgs& a, int tile, int sig, C* sm) {
   const C* __restrict__ tw = static_cast<const C*>(a.tw);
-  const C* __restrict__ in = static_cast<const C*>(a.in) + (int64_t)blockIdx.y * a.m;
-  C* __restrict__ out = static_cast<C*>(a.out) + (int64_t)blockIdx.y * a.m;
-  const int p0 = blockIdx.x * a.T;
+  const C* __restrict__ in = static_cast<const C*>(a.in) + (int64_t)sig * a.m;
+  C* __restrict__ out = static_cast<C*>(a.out) + (int64_t)sig * a.m;
+  const int p0 = tile * a.T;
   const int n = a.T * a.LB;
   const int d = a.d;
   const int nthr = blockDim.x;
   // blockDim.x is a multiple of T, so each thread keeps one column.
   const int tcol = a.divT.mod(threadIdx.x);
+  // the last CTA may hold fewer than T columns (T need not divide nD)
+  const int nvalid = min(a.T, a.nD - p0);
+  const int n_ok = tcol < nvalid ? n : 0;
   int off[kMaxSub];
 #pragma unroll
   for (int s = 0; s < kMaxSub; ++s)
     off[s] = (s < a.nsub) ? int((int64_t(tcol) * a.alpha[s]) % a.sub_n[s]) : 0;
   int et[4];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) et[r] = (r < d) ? __ldg(a.Etab + (p0 + tcol) * a.ts + r) : 0;
+  for (int r = 0; r < 4; ++r) et[r] = (r < d && n_ok) ? __ldg(a.Etab + (p0 + tcol) * a.ts + r) : 0;
   constexpr int CH = EPT / 2;  // loads in flight per thread per chunk
   const bool ws_in = a.load_mode == MAP_WS;
 #pragma unroll
@@ -261,7 +359,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) col_pass_kernel(PassArgs a) {
   for (int k = 0; k < CH; ++k) {
     const int w = threadIdx.x + (k0 + k) * nthr;
     sidx[k] = -1;
-    if (w < n) {
+    if (w < n_ok) {
       const int j = a.divT.div(w);
       if (ws_in) {
         v[k] = __ldg(in + j * a.nD + p0 + tcol);
@@ -290,7 +388,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) col_pass_kernel(PassArgs a) {
   for (int k = 0; k < CH; ++k) {
     const int w = threadIdx.x + (k0 + k) * nthr;
     gidx[k] = -1;
-    if (w < n) {
+    if (w < n_ok) {
       const int j = a.divT.div(w);
       if (ws_out) {
         v[k] = sm[phys(j * a.T + tcol)];
@@ -306,6 +404,18 @@ __global__ void __launch_bounds__(kMaxThreads, 1) col_pass_kernel(PassArgs a) {
   for (int k = 0; k < CH; ++k)
     if (gidx[k] >= 0) out[gidx[k]] = v[k];
   }
+}
+
+template <typename C, int EPT, bool POW2>
+__global__ void __launch_bounds__(kMaxThreads, 1) row_pass_kernel(PassArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  row_pass_body<C, EPT, POW2>(a, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
+}
+
+template <typename C, int EPT, bool POW2>
+__global__ void __launch_bounds__(kMaxThreads, 1) col_pass_kernel(PassArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  col_pass_body<C, EPT, POW2>(a, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
 }
 
 // Allow the largest dynamic shared-memory size and prefer the maximum shared

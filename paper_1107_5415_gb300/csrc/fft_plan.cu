@@ -14,43 +14,31 @@
 #include "fft_plan.hpp"
 #include "lattice.hpp"
 #include "plan_common.hpp"
+#include "plan_internal.hpp"
 
 using namespace pfft;
 
-struct pfft_plan_s {
-  int d = 0;
-  int64_t batch = 0;
-  int dtype = 0;
-  IMat M, H, G;
-  i64 m = 0;
-  std::vector<i64> eps;                 // all d elementary divisors
-  int D = 0;                            // non-trivial cycles
-  std::vector<int> n;                   // their lengths, ascending
-  std::vector<std::vector<i64>> LAM;    // D rows: lambda_j(y) = LAM_j . y mod n_j
-  std::vector<std::vector<i64>> MU;     // D rows: mu_j(k) = MU_j . k mod n_j
-  int nD = 1, LB = 1;      // row length and number of rows of the logical LB x nD array
-  std::vector<int> pen;     // column-pass pencil axes (row-major), product LB
-  int fs_na = 1;            // four-step split of a long last cycle: n = fs_na * nD
-  i64 fs_N = 1;             // the full length of the last cycle
-  void* fs_tab = nullptr;   // exp(-2 pi i t / fs_N), two-level table
-  // device state
-  int device = 0;
-  int* dtab = nullptr;
-  void* tw = nullptr;
-  void* ws = nullptr;
-  void* stw = nullptr;  // stage twiddle tables of the register-resident passes
-  int* runs = nullptr;  // bulk-copy runs of the row pass
-  int* status = nullptr;  // device status word
-  PassArgs rowp{}, colp{};
-  Profiler prof;
-};
-
 namespace {
 
-// Radices for a cycle length: 16s first, then the rest of the power of two,
-// then odd primes.  Returns false if a prime factor is not supported.
+// Radices for a cycle length: primes from 11 up first (direct stages, up to
+// kMaxDirectRadix), then 16s, the rest of the power of two and 3, 5, 7 -- the
+// execution order of the stage regions.  Returns false if a prime factor is
+// not supported.
 bool factor_radices(int n, std::vector<int>& out) {
   out.clear();
+  for (int p = kMinDirectRadix; p <= kMaxDirectRadix && p <= n; p += 2) {
+    bool prime = true;
+    for (int q = 3; q * q <= p; q += 2)
+      if (p % q == 0) {
+        prime = false;
+        break;
+      }
+    if (!prime) continue;
+    while (n % p == 0) {
+      out.push_back(p);
+      n /= p;
+    }
+  }
   int p2 = 0;
   while (n % 2 == 0) {
     n /= 2;
@@ -63,7 +51,7 @@ bool factor_radices(int n, std::vector<int>& out) {
   if (p2 == 3) out.push_back(8);
   if (p2 == 2) out.push_back(4);
   if (p2 == 1) out.push_back(2);
-  static const int primes[] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
+  static const int primes[] = {3, 5, 7};
   for (int p : primes)
     while (n % p == 0) {
       out.push_back(p);
@@ -85,7 +73,8 @@ void set_box(BoxDesc& B, const IMat& H) {
 }
 
 // Stages of a Stockham DFT along one pencil axis of length a and stride
-// sigma, in the radix order of kRadixOrder (Ns accumulates in that order).
+// sigma, in the radix order of kRadixOrder (Ns accumulates in that order);
+// twiddles come from a table of order nD (a multiple of a).
 bool axis_stages(std::vector<StageDesc>& out, int a, int sigma, int nD) {
   std::vector<int> rad;
   if (!factor_radices(a, rad)) return false;
@@ -109,16 +98,22 @@ bool axis_stages(std::vector<StageDesc>& out, int a, int sigma, int nD) {
 }
 
 int radix_region(int R) {
-  for (int i = 0; i < 14; ++i)
+  for (int i = 0; i < kDirectRegion; ++i)
     if (kRadixOrder[i] == R) return i;
-  return -1;
+  return R >= kMinDirectRadix && R <= kMaxDirectRadix ? kDirectRegion : -1;
+}
+
+// Execution order of the regions: direct prime stages first.
+int region_rank(int R) {
+  const int reg = radix_region(R);
+  return reg == kDirectRegion ? -1 : reg;
 }
 
 // Merge the stages of all axes, grouped by radix region (stable, so each
 // axis keeps its own order), and fill the per-region counts.
 bool set_stages(PassArgs& p, std::vector<StageDesc> all) {
   std::stable_sort(all.begin(), all.end(), [](const StageDesc& x, const StageDesc& y) {
-    return radix_region(x.R) < radix_region(y.R);
+    return region_rank(x.R) < region_rank(y.R);
   });
   if (all.size() > size_t(kMaxStages)) return false;
   p.nstages = int(all.size());
@@ -139,6 +134,12 @@ int threads_for(const PassArgs& p, int ept) {
   int need = (p.T * p.L + ept - 1) / ept;
   for (int i = 0; i < p.nstages; ++i) {
     const int R = p.st[i].R;
+    if (radix_region(R) == kDirectRegion) {  // (R + 1) / 2 output pairs per butterfly
+      const int items = p.T * (p.L / R) * ((R + 1) / 2);
+      const int cap = ept / 2 + 2;  // kDirectItems
+      need = std::max(need, (items + cap - 1) / cap);
+      continue;
+    }
     const int nb = std::max(1, ept / R);
     const int bfly = p.T * p.L / R;
     need = std::max(need, (bfly + nb - 1) / nb);
@@ -148,6 +149,22 @@ int threads_for(const PassArgs& p, int ept) {
 }
 
 size_t elem_bytes(int dtype) { return dtype == PFFT_C64 ? 8 : 16; }
+
+// Whether one pencil of length L fits a CTA of the shared-memory kernels:
+// at most `row_max` elements and kMaxThreads threads for its stages.
+bool tile_fits(int L, int row_max, int ept) {
+  if (L > row_max) return false;
+  std::vector<int> rad;
+  if (!factor_radices(L, rad)) return false;
+  PassArgs p;
+  std::memset(&p, 0, sizeof(p));
+  p.T = 1;
+  p.L = L;
+  p.nstages = int(rad.size());
+  if (p.nstages > kMaxStages) return false;
+  for (int i = 0; i < p.nstages; ++i) p.st[i].R = rad[i];
+  return threads_for(p, ept) <= kMaxThreads;
+}
 
 pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) {
   const int ept = P.dtype == PFFT_C64 ? 32 : 16;
@@ -167,10 +184,10 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
     p.L = P.LB;
     int sigma = 1;
     for (int s = int(P.pen.size()) - 1; s >= 0; --s) {  // pencil axes, last fastest
-      if (!axis_stages(stg, P.pen[s], sigma, P.nD)) return PFFT_ERR_UNSUPPORTED;
+      if (!axis_stages(stg, P.pen[s], sigma, p.tw_n)) return PFFT_ERR_UNSUPPORTED;
       sigma *= P.pen[s];
     }
-    p.groups = P.nD / T;
+    p.groups = (P.nD + T - 1) / T;
   }
   if (!set_stages(p, stg)) return PFFT_ERR_UNSUPPORTED;
   p.divT.init(uint32_t(T));
@@ -182,7 +199,7 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
     const int Rm = P.dtype == PFFT_C64 ? 32 : 16;
     const int L = p.L;
     const bool pow2L = L >= Rm && (L & (L - 1)) == 0 && (T & (T - 1)) == 0;
-    p.fast = (p.pow2 && pow2L && P.d <= 3 && (!cols || P.pen.size() == 1) && T * L <= (P.dtype == PFFT_C64 ? 16384 : 8192)) ? 1 : 0;
+    p.fast = (!P.generic_only && p.tw_n == P.nD && p.pow2 && pow2L && P.d <= 3 && (!cols || P.pen.size() == 1) && T * L <= (P.dtype == PFFT_C64 ? 16384 : 8192)) ? 1 : 0;
     if (p.fast) {
       int lg = 0, lr = 0;
       while ((1 << lg) < L) ++lg;
@@ -208,7 +225,11 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
   p.nthreads = threads_for(p, ept);
   if (p.nthreads > kMaxThreads) return PFFT_ERR_UNSUPPORTED;
   const int nel = T * p.L;
-  p.smem_bytes = int(size_t((nel - 1) + ((nel - 1) >> 4) + 1) * elem_bytes(P.dtype));
+  int rmax = 0;  // omega_R table of the direct stages, after the tile
+  for (int i = 0; i < p.nstages; ++i)
+    if (radix_region(p.st[i].R) == kDirectRegion) rmax = std::max(rmax, p.st[i].R);
+  p.dir_off = (nel - 1) + ((nel - 1) >> 4) + 1;
+  p.smem_bytes = int(size_t(p.dir_off + rmax) * elem_bytes(P.dtype));
   if (p.smem_bytes > 227 * 1024) return PFFT_ERR_UNSUPPORTED;
   return PFFT_OK;
 }
@@ -219,7 +240,7 @@ pfft_status choose_and_configure(PassArgs& p, const pfft_plan_s& P, bool cols, i
   const int L = cols ? P.LB : P.nD;
   const int limit = cols ? P.nD : P.LB;
   int T = 1;
-  while (T * 2 <= cap && T * 2 <= limit && T * 2 * L <= budget && (!cols || P.nD % (T * 2) == 0)) T *= 2;
+  while (T * 2 <= cap && T * 2 <= limit && T * 2 * L <= budget) T *= 2;
   for (;;) {
     pfft_status st = configure_pass(p, P, cols, T);
     if (st == PFFT_OK) return st;
@@ -231,7 +252,7 @@ pfft_status choose_and_configure(PassArgs& p, const pfft_plan_s& P, bool cols, i
 }  // namespace
 
 // ----------------------------------------------------------------- planning
-static pfft_status plan_host(pfft_plan_s& P, int d, const int64_t* Mv) {
+pfft_status pfft::plan_host(pfft_plan_s& P, int d, const int64_t* Mv) {
   if (d < 1 || d > 4) return PFFT_ERR_ARG;
   P.d = d;
   P.M = IMat(d);
@@ -311,15 +332,15 @@ static pfft_status plan_host(pfft_plan_s& P, int d, const int64_t* Mv) {
   // length-n_b DFTs (twiddle exp(-2 pi i lambda_a mu_b / n) between the passes)
   // and lambda_a becomes one more pencil axis of the column pass.
   const int row_max = P.dtype == PFFT_C64 ? 16384 : 8192;
-  if (P.fs_N > row_max) {
+  const int ept = P.dtype == PFFT_C64 ? 32 : 16;
+  if (P.fs_N > 1 && !tile_fits(int(std::min<i64>(P.fs_N, row_max + 1)), row_max, ept)) {
     const i64 other = P.m / P.fs_N;
-    std::vector<int> rad;
     int best = 0;
-    for (i64 nb = row_max; nb >= 2; --nb) {
+    for (i64 nb = std::min<i64>(row_max, P.fs_N - 1); nb >= 2; --nb) {
       if (P.fs_N % nb) continue;
       const i64 na = P.fs_N / nb;
-      if (!factor_radices(int(nb), rad) || na > row_max || !factor_radices(int(na), rad)) continue;
-      if (other * na > row_max) continue;
+      if (other * na > row_max || !tile_fits(int(nb), row_max, ept) || !tile_fits(int(other * na), row_max, ept))
+        continue;
       best = int(nb);
       break;
     }
@@ -359,7 +380,7 @@ std::vector<i64> combo(const std::vector<std::vector<i64>>& gens, const std::vec
 }
 }  // namespace
 
-static pfft_status plan_device(pfft_plan_s& P) {
+pfft_status pfft::plan_device(pfft_plan_s& P) {
   const int d = P.d, D = P.D;
   if (cudaGetDevice(&P.device) != cudaSuccess) return PFFT_ERR_CUDA;
   if (D == 0) return PFFT_OK;  // m == 1: the transform is the identity
@@ -453,19 +474,33 @@ static pfft_status plan_device(pfft_plan_s& P) {
     PIi[e] = PIinv[e];
     PIf[e] = PI[e];
   }
-  if (int e_ = device_alloc((void**)&P.dtab, tab.size() * sizeof(int))) return pfft_status(e_);
+  if (int e_ = P.alloc((void**)&P.dtab, tab.size() * sizeof(int))) return pfft_status(e_);
   if (cudaMemcpy(P.dtab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
     return PFFT_ERR_CUDA;
   const size_t eb = elem_bytes(P.dtype);
-  if (int e_ = device_alloc((void**)&P.tw, size_t(nD) * eb)) return pfft_status(e_);
-  if (int e_ = device_alloc((void**)&P.status, sizeof(int))) return pfft_status(e_);
+  if (int e_ = P.alloc((void**)&P.tw, size_t(nD) * eb)) return pfft_status(e_);
+  if (int e_ = P.alloc((void**)&P.status, sizeof(int))) return pfft_status(e_);
   cudaMemset(P.status, 0, sizeof(int));
   if (launch_twiddles(P.tw, nD, P.dtype, 0) != 0) return PFFT_ERR_CUDA;
-  if (npen >= 1)
-    if (int e_ = device_alloc(&P.ws, size_t(P.m) * P.batch * eb)) return pfft_status(e_);
+  // The column pass transforms the pencil axes; their twiddles come from the
+  // nD table when every axis divides nD (always, unless the last cycle is
+  // split four-step: n_a need not divide n_b), else from a table of order
+  // lcm(axes) <= LB.
+  int col_n = nD;
+  {
+    i64 l = 1;
+    for (int a : P.pen) l = l / gcd64(l, a) * a;
+    if (npen >= 1 && nD % l != 0) {
+      col_n = int(l);
+      if (int e_ = P.alloc(&P.tw_col, size_t(col_n) * eb)) return pfft_status(e_);
+      if (launch_twiddles(P.tw_col, col_n, P.dtype, 0) != 0) return PFFT_ERR_CUDA;
+    }
+  }
+  if (npen >= 1 && P.own_workspace)
+    if (int e_ = P.alloc(&P.ws, size_t(P.m) * P.batch * eb)) return pfft_status(e_);
   if (na > 1) {  // exp(-2 pi i t / n) for t < n, as lo[t & 2047] * hi[t >> 11]
     const int nhi = int((P.fs_N + 2047) >> 11);
-    if (int e_ = device_alloc(&P.fs_tab, size_t(2048 + nhi) * eb)) return pfft_status(e_);
+    if (int e_ = P.alloc(&P.fs_tab, size_t(2048 + nhi) * eb)) return pfft_status(e_);
     if (launch_phase_tables(P.fs_tab, P.fs_N, nhi, P.dtype, 0) != 0) return PFFT_ERR_CUDA;
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return PFFT_ERR_CUDA;
@@ -532,7 +567,9 @@ static pfft_status plan_device(pfft_plan_s& P) {
     p->Etab = Etab - tab.data() + P.dtab;
     p->PIinv = PIi - tab.data() + P.dtab;
     p->PI = PIf - tab.data() + P.dtab;
-    p->tw = P.tw;
+    const bool colt = (p == &P.colp) && P.tw_col;
+    p->tw = colt ? P.tw_col : P.tw;
+    p->tw_n = colt ? col_n : nD;
     p->ts = ts;
     p->status = P.status;
     set_box(p->boxH, P.H);
@@ -616,7 +653,7 @@ static pfft_status plan_device(pfft_plan_s& P) {
       for (int r = 0; r < LB; ++r)
         for (size_t j = 0; j < per[r].size(); ++j)
           for (int k = 0; k < 4; ++k) flat[(size_t(r) * maxr + j) * 4 + k] = per[r][j][k];
-      if (int e_ = device_alloc((void**)&P.runs, flat.size() * sizeof(int))) return pfft_status(e_);
+      if (int e_ = P.alloc((void**)&P.runs, flat.size() * sizeof(int))) return pfft_status(e_);
       cudaMemcpy(P.runs, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice);
       P.rowp.tma = 1;
       P.rowp.runs = P.runs;
@@ -628,7 +665,7 @@ static pfft_status plan_device(pfft_plan_s& P) {
   if (!idx.empty()) {
     int* didx = nullptr;
     if (int e_ = device_alloc((void**)&didx, idx.size() * sizeof(int))) return pfft_status(e_);
-    if (int e_ = device_alloc(&P.stw, idx.size() * eb)) {
+    if (int e_ = P.alloc(&P.stw, idx.size() * eb)) {
       cudaFree(didx);
       return pfft_status(e_);
     }
@@ -643,17 +680,22 @@ static pfft_status plan_device(pfft_plan_s& P) {
   return PFFT_OK;
 }
 
-static void release(pfft_plan_s* P) {
+pfft_status pfft::plan_retile(pfft_plan_s& P, int row_budget, int col_budget) {
+  if (!P.generic_only || P.D == 0) return PFFT_ERR_ARG;
+  pfft_status st = choose_and_configure(P.rowp, P, false, 64, std::max(row_budget, P.nD));
+  if (st != PFFT_OK || P.pen.empty()) return st;
+  return choose_and_configure(P.colp, P, true, 16, std::max(col_budget, P.LB));
+}
+
+void pfft::plan_release(pfft_plan_s* P) {
   if (!P) return;
-  if (P->dtab) cudaFree(P->dtab);
-  if (P->tw) cudaFree(P->tw);
-  if (P->ws) cudaFree(P->ws);
-  if (P->stw) cudaFree(P->stw);
-  if (P->fs_tab) cudaFree(P->fs_tab);
-  if (P->runs) cudaFree(P->runs);
-  if (P->status) cudaFree(P->status);
+  if (!P->arena) {
+    for (void* p : {(void*)P->dtab, P->tw, P->tw_col, P->ws, P->stw, P->fs_tab, (void*)P->runs, (void*)P->status})
+      if (p) cudaFree(p);
+  }
   delete P;
 }
+static void release(pfft_plan_s* P) { plan_release(P); }
 
 extern "C" pfft_status pfft_plan_create(pfft_plan* out, int d, const int64_t* M, int64_t batch,
                                         int dtype, unsigned flags) {

@@ -31,7 +31,18 @@ enum MapMode { MAP_WS = 0, MAP_BOX_H = 1, MAP_BOX_G = 2 };
 constexpr int kMaxStages = 16;
 constexpr int kMaxSub = 3;
 constexpr int kMaxThreads = 512;
-constexpr int kRadixOrder[14] = {16, 8, 4, 2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
+constexpr int kRadixOrder[7] = {16, 8, 4, 2, 3, 5, 7};
+// Stages of a prime radix from 11 up are evaluated directly from shared
+// memory (run_direct_stage; a register butterfly of that size spills); they
+// run before all others, so the first one of each axis needs no twiddles.
+constexpr int kDirectRegion = 7;
+constexpr int kMinDirectRadix = 11;
+constexpr int kMaxDirectRadix = 1021;
+// Output pairs a thread holds in a direct stage: a butterfly of radix R >= 11
+// has (R + 1) / 2 <= 6R / 11 pairs, so EPT / 2 + 2 covers a tile of EPT
+// elements per thread.
+template <int EPT>
+constexpr int kDirectItems = EPT / 2 + 2;
 
 // One radix stage of a Stockham autosort DFT along one axis of a pencil.
 struct StageDesc {
@@ -40,11 +51,11 @@ struct StageDesc {
   int aR;      // a / R
   int sigma;   // stride of the axis inside the pencil (elements)
   int Ns;      // product of the radices of the earlier stages on this axis
-  int twstep;  // nD / (Ns * R): index step into the omega_{nD} table
+  int twstep;  // tw_n / (Ns * R): index step into the pass's omega_{tw_n} table
   FastDiv div_aR, div_sigma, div_Ns;
 };
 
-struct PassArgs {
+struct alignas(16) PassArgs {
   // geometry
   int L;        // pencil length (row pass: nD; column pass: LB)
   int T;        // pencils per CTA
@@ -52,7 +63,8 @@ struct PassArgs {
   int ts;       // int32 per table entry: 2 (d <= 2) or 4 (d = 3, 4)
   int cols;     // 1: column pass, 0: row pass
   int nstages;
-  int cnt[14];  // stages per radix, in the order of kRadixOrder
+  int cnt[8];  // stages per radix, in the order of kRadixOrder; [7]: direct prime stages
+  int dir_off;  // shared-memory element offset of the omega_R table of a direct stage
   int pow2;     // all radices are powers of two
   int fast;       // 1: use the register-resident power-of-two kernels (fft_fast.cuh)
   int fast_tail;  // radix of the first stage (1 = none)
@@ -93,6 +105,9 @@ struct PassArgs {
   double scale;
   const void* in;
   void* out;
+  // grouped launches: in / out hold byte offsets into the launch's base
+  // pointer number in_sel / out_sel (see batch_kernels.cu)
+  int in_sel, out_sel;
   // tables (device, d int32 per entry)
   const int* Atab;   // [LB]  box(H) point of sum_{j<D} lambda_j g_j
   const int* Btab;   // [nD]  box(H) point of lambda_D g_D
@@ -100,7 +115,8 @@ struct PassArgs {
   const int* Etab;   // [nD]  box(G) point of PIinv[pos] h_D   (indexed by position)
   const int* PIinv;  // [nD]  column position -> mu_D (or lambda_D)
   const int* PI;     // [nD]  mu_D -> column position
-  const void* tw;    // [nD]  omega_{nD}^t = exp(-2 pi i t / nD)
+  const void* tw;    // [tw_n] omega_{tw_n}^t = exp(-2 pi i t / tw_n)
+  int tw_n;          // order of tw: nD (row pass); a common multiple of the pencil axes (column pass)
   BoxDesc boxH, boxG;
   // shear of the column pass: a run of consecutive output slots along the
   // fastest output coordinate visits (mu_<D + t alpha, position + t).

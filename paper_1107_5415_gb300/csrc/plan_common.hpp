@@ -16,6 +16,39 @@ inline int device_alloc(void** p, size_t bytes) {
   return e == cudaErrorMemoryAllocation ? 6 /* PFFT_ERR_OOM */ : 7 /* PFFT_ERR_CUDA */;
 }
 
+// Bump allocator over large device chunks: the tables of many small plans
+// (a batch of patterns) without one cudaMalloc each.  Freed all at once.
+class Arena {
+ public:
+  int alloc(void** p, size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (chunks_.empty() || used_ + bytes > cap_) {
+      const size_t c = bytes > kChunk ? bytes : kChunk;
+      void* q = nullptr;
+      if (int e = device_alloc(&q, c)) return e;
+      chunks_.push_back(q);
+      cap_ = c;
+      used_ = 0;
+    }
+    *p = static_cast<char*>(chunks_.back()) + used_;
+    used_ += bytes;
+    return 0;
+  }
+  size_t reserved() const {
+    size_t s = 0;
+    for (size_t i = 0; i + 1 < chunks_.size(); ++i) s += kChunk;
+    return s + cap_;
+  }
+  ~Arena() {
+    for (void* c : chunks_) cudaFree(c);
+  }
+
+ private:
+  static constexpr size_t kChunk = size_t(64) << 20;
+  std::vector<void*> chunks_;
+  size_t used_ = 0, cap_ = 0;
+};
+
 // Per-kernel timing with CUDA events recorded on the launching stream.
 class Profiler {
  public:

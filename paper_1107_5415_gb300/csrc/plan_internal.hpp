@@ -1,0 +1,58 @@
+// The transform plan (host planner state and device tables), shared by the
+// single-pattern entry points (fft_plan.cu) and the many-pattern batch
+// (batch.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/pfft.h"
+#include "fft_plan.hpp"
+#include "lattice.hpp"
+#include "plan_common.hpp"
+
+struct pfft_plan_s {
+  int d = 0;
+  int64_t batch = 0;
+  int dtype = 0;
+  pfft::IMat M, H, G;
+  pfft::i64 m = 0;
+  std::vector<pfft::i64> eps;                 // all d elementary divisors
+  int D = 0;                                  // non-trivial cycles
+  std::vector<int> n;                         // their lengths, ascending
+  std::vector<std::vector<pfft::i64>> LAM;    // D rows: lambda_j(y) = LAM_j . y mod n_j
+  std::vector<std::vector<pfft::i64>> MU;     // D rows: mu_j(k) = MU_j . k mod n_j
+  int nD = 1, LB = 1;       // row length and number of rows of the logical LB x nD array
+  std::vector<int> pen;     // column-pass pencil axes (row-major), product LB
+  int fs_na = 1;            // four-step split of a long last cycle: n = fs_na * nD
+  pfft::i64 fs_N = 1;       // the full length of the last cycle
+  void* fs_tab = nullptr;   // exp(-2 pi i t / fs_N), two-level table
+  // options (set before plan_device)
+  pfft::Arena* arena = nullptr;  // sub-allocate device tables here (batch plans)
+  bool generic_only = false;     // shared-memory Stockham kernels only (grouped launches)
+  bool own_workspace = true;     // allocate the LB x nD workspace
+  // device state
+  int device = 0;
+  int* dtab = nullptr;
+  void* tw = nullptr;
+  void* tw_col = nullptr;  // column-pass table when its axes do not divide nD (split last cycle)
+  void* ws = nullptr;
+  void* stw = nullptr;  // stage twiddle tables of the register-resident passes
+  int* runs = nullptr;  // bulk-copy runs of the row pass
+  int* status = nullptr;  // device status word
+  pfft::PassArgs rowp{}, colp{};
+  pfft::Profiler prof;
+
+  int alloc(void** p, size_t bytes) { return arena ? arena->alloc(p, bytes) : pfft::device_alloc(p, bytes); }
+};
+
+namespace pfft {
+// Exact integer planning (HNF, SNF, cycle split); no device work.
+pfft_status plan_host(pfft_plan_s& P, int d, const int64_t* M);
+// Device tables and pass descriptors.
+pfft_status plan_device(pfft_plan_s& P);
+// Re-choose the tiles of both passes (pencils per CTA) under the given
+// element budgets; generic kernels only.  Tables are unchanged.
+pfft_status plan_retile(pfft_plan_s& P, int row_budget, int col_budget);
+void plan_release(pfft_plan_s* P);
+}  // namespace pfft

@@ -37,177 +37,11 @@
 
 #include "../../include/pfft.h"
 #include "device_common.cuh"
+#include "wavelet_kernels.cuh"
 #include "lattice.hpp"
 #include "plan_common.hpp"
 
 namespace pfft {
-
-constexpr int kLoBits = 11;
-
-struct LevelDesc {
-  int d;
-  int mN;                // points of G(N^T)
-  int mM;                // points of G(M^T)
-  BoxDesc HM;            // box of H(M^T)
-  int HNext[4];          // extents of the box of H(N^T)
-  FastDiv divHN[4];
-  int shift1[4];         // box(H(M^T)) point of N^T l1
-  long long adjMT[16];   // adj(M^T)
-  long long q;           // |det M|
-  int sM;                // sign det M
-  int J[16];
-  long long adjJT[16];
-  int aJ;                // |det J|
-  long long phw[4];      // adj(M) (J z): phase numerator of h is sM * h . phw mod q
-  int symbol;
-  double eta;
-  long long K[16];       // sign(det M) J^T adj(M^T): N^{-T} h = K h / q
-  int K32[16];           // the same in int32 when `small`
-  int small;             // |K h| < 2^30 for every box point h: int32 arithmetic
-  int vpar[4];           // parity vector of J^T Z^d
-  FastDiv div2q;         // division by 2q (int32 path)
-  int off2q;             // multiple of 2q that makes K h non-negative (int32 path)
-  int ph32[4];           // sign(det M) adj(M) (J z) mod q (int32 path)
-  FastDiv divq;          // division by q (int32 path)
-  int offq;              // multiple of q that makes ph32 . h non-negative
-  const void* tab_lo;    // exp(-2 pi i t / q), t < 2^kLoBits
-  const void* tab_hi;    // exp(-2 pi i (t << kLoBits) / q)
-};
-
-// Periodised weight w(N^{-T} h) of the point h (see the header comment);
-// the fibre partner has weight 1 - w.
-template <typename Rl, bool SMALL>
-__device__ __forceinline__ Rl fibre_weight(const LevelDesc& L, const int* h) {
-  using I = typename std::conditional<SMALL, int, long long>::type;
-  const int d = L.d;
-  const I q = I(L.q);
-  Rl prod = Rl(1);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (j >= d) break;
-    I t;  // numerator of (N^{-T} h)_j mod 2, in [0, 2q)
-    if constexpr (SMALL) {
-      int acc = L.off2q;
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (i < d) acc += L.K32[j * d + i] * h[i];
-      t = L.div2q.mod(acc);
-    } else {
-      long long acc = 0;
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (i < d) acc += L.K[j * d + i] * (long long)h[i];
-      t = acc % (2 * q);
-      if (t < 0) t += 2 * q;
-    }
-    Rl U = Rl(0);
-#pragma unroll
-    for (int n = 0; n >= -2; --n) {  // shifts with |t/q + n| possibly < 1
-      const I sn = t + I(n) * q;
-      const I an = sn < 0 ? -sn : sn;
-      Rl b;
-      if (L.symbol == PWT_DIRICHLET) {
-        b = (2 * an < q) ? Rl(1) : (2 * an == q) ? Rl(0.5) : Rl(0);
-      } else {
-        const Rl eta = Rl(L.eta);
-        b = (Rl(0.5) * (Rl(1) + eta) - Rl(an) / Rl(q)) / eta;
-        b = b < Rl(0) ? Rl(0) : (b > Rl(1) ? Rl(1) : b);
-      }
-      U += ((L.vpar[j] & n) & 1) ? -b : b;
-    }
-    prod *= U;
-  }
-  return Rl(0.5) * (Rl(1) + prod);
-}
-
-template <typename C, bool TAB = true, bool SMALL = false>
-__device__ __forceinline__ C wavelet_phase(const LevelDesc& L, const int* h) {
-  long long t = 0;
-  if constexpr (SMALL) {
-    int acc = L.offq;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (i < L.d) acc += L.ph32[i] * h[i];
-    t = L.divq.mod(acc);
-  } else {
-#pragma unroll
-    for (int i = 0; i < 4; ++i)  // each product < 2^62; reduce term by term
-      if (i < L.d) t += ((long long)h[i] * L.phw[i]) % L.q;
-    t = (L.sM * t) % L.q;
-    if (t < 0) t += L.q;
-  }
-  if constexpr (!TAB) {
-    // no tables: single-precision sincospi of the exactly reduced fraction t / q
-    using Rl = decltype(C::x);
-    float sn, cs;
-    sincospif(2.0f * (float(t) / float(L.q)), &sn, &cs);
-    return cmake<C>(Rl(cs), Rl(-sn));
-  }
-  const C* lo = static_cast<const C*>(L.tab_lo);
-  const C* hi = static_cast<const C*>(L.tab_hi);
-  return cmul(hi[t >> kLoBits], lo[t & ((1 << kLoBits) - 1)]);
-}
-
-// mode 0: decompose c -> (d1, d2); 1: reconstruct; 2: adjoint.  One thread
-// per fibre g (grid-stride over the slots of one signal, blockIdx.y = signal).
-template <typename C, int MODE, bool TAB = true, bool SMALL = false>
-__global__ void __launch_bounds__(256) split_kernel(LevelDesc L, int batch, const C* __restrict__ cin,
-                                                    C* __restrict__ cout, const C* __restrict__ d1in,
-                                                    const C* __restrict__ d2in, C* __restrict__ d1out,
-                                                    C* __restrict__ d2out) {
-  using Rl = decltype(C::x);
-  (void)batch;
-  const int b = blockIdx.y;
-  for (int gs = blockIdx.x * blockDim.x + threadIdx.x; gs < L.mN; gs += gridDim.x * blockDim.x) {
-    int g[4] = {0, 0, 0, 0}, h1[4] = {0, 0, 0, 0};
-    int s = gs;
-    for (int r = L.d - 1; r >= 0; --r) {
-      const int qd = L.divHN[r].div(s);
-      g[r] = s - qd * L.HNext[r];
-      s = qd;
-    }
-    int slot0 = 0;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      if (r < L.d) {
-        h1[r] = g[r] + L.shift1[r];
-        slot0 += g[r] * L.HM.stride[r];
-      }
-    }
-    box_fix(L.HM, h1);
-    int slot1 = 0;
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-      if (r < L.d) slot1 += h1[r] * L.HM.stride[r];
-    const Rl w0 = fibre_weight<Rl, SMALL>(L, g);
-    const Rl w1 = Rl(1) - w0;
-    Rl A0, A1;
-    if (L.symbol == PWT_DIRICHLET) {
-      A0 = sqrt(Rl(2) * w0);
-      A1 = sqrt(Rl(2) * w1);
-    } else {
-      A0 = Rl(1.41421356237309504880) * w0;
-      A1 = Rl(1.41421356237309504880) * w1;
-    }
-    // B(h0) = A(h1) e(h0), B(h1) = A(h0) e(h1), e(h1) = -e(h0)
-    const C e0 = wavelet_phase<C, TAB, SMALL>(L, g);
-    const Rl r2 = Rl(0.70710678118654752440);
-    const long long oM = (long long)b * L.mM, oN = (long long)b * L.mN;
-    if (MODE == 0) {
-      const C c0 = cin[oM + slot0], c1 = cin[oM + slot1];
-      d1out[oN + gs] = cscale(cadd(cscale(c0, A0), cscale(c1, A1)), r2);
-      // conj(B0) c0 + conj(B1) c1 = conj(e0) (A1 c0 - A0 c1)
-      d2out[oN + gs] = cscale(cmul(cconj(e0), csub(cscale(c0, A1), cscale(c1, A0))), r2);
-    } else {
-      const C a = d1in[oN + gs], bb = d2in[oN + gs];
-      const Rl S = A0 * A0 + A1 * A1;
-      const Rl fac = (MODE == 1) ? Rl(1.41421356237309504880) / S : r2;
-      const C eb = cmul(e0, bb);
-      cout[oM + slot0] = cscale(cadd(cscale(a, A0), cscale(eb, A1)), fac);
-      cout[oM + slot1] = cscale(csub(cscale(a, A1), cscale(eb, A0)), fac);
-    }
-  }
-}
 
 template <typename C>
 __global__ void phase_table_kernel(C* lo, C* hi, long long q, int nhi) {
@@ -609,6 +443,30 @@ extern "C" pfft_status pwt_reconstruct(pwt_plan p, const void* scaling, const vo
 extern "C" pfft_status pwt_adjoint(pwt_plan p, const void* scaling, const void* const* wavelets,
                                    void* c_hat, void* stream) {
   return synthesise(p, scaling, wavelets, c_hat, stream, 2);
+}
+
+// Descriptor of one split level of M by J (host only; for batch plans, whose
+// kernels evaluate the phases without tables).
+pfft_status pfft::describe_split_level(int d, const int64_t* M, const int64_t* J, int symbol, double eta,
+                                       LevelDesc* out) {
+  if (!M || !J || !out || d < 1 || d > 4 || (symbol != PWT_DIRICHLET && symbol != PWT_DLVP) ||
+      (symbol == PWT_DLVP && !(eta > 0.0 && eta < 1.0)))
+    return PFFT_ERR_ARG;
+  pwt_plan_s P;
+  P.d = d;
+  P.levels = 1;
+  P.symbol = symbol;
+  P.eta = eta;
+  P.batch = 1;
+  P.dtype = PFFT_C64;
+  pfft_status st;
+  try {
+    st = plan_levels(P, M, J);
+  } catch (const LatticeError& e) {
+    st = pfft_status(e.code);
+  }
+  if (st == PFFT_OK) *out = P.lv[0];
+  return st;
 }
 
 // ---------------------------------------------------------------------------

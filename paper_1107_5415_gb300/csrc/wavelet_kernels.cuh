@@ -1,0 +1,204 @@
+// Device side of the wavelet split step (Section 5.3, step 4): the level
+// descriptor, the periodised symbol weights, the wavelet phase and the
+// per-fibre butterfly, shared by the plan-based launches (wavelet.cu) and the
+// grouped launches of pattern batches (batch_kernels.cu).  The derivation of
+// the symbol evaluation is given at the top of wavelet.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "../../include/pfft.h"
+#include "device_common.cuh"
+
+namespace pfft {
+
+constexpr int kLoBits = 11;
+
+struct LevelDesc {
+  int d;
+  int mN;                // points of G(N^T)
+  int mM;                // points of G(M^T)
+  BoxDesc HM;            // box of H(M^T)
+  int HNext[4];          // extents of the box of H(N^T)
+  FastDiv divHN[4];
+  int shift1[4];         // box(H(M^T)) point of N^T l1
+  long long adjMT[16];   // adj(M^T)
+  long long q;           // |det M|
+  int sM;                // sign det M
+  int J[16];
+  long long adjJT[16];
+  int aJ;                // |det J|
+  long long phw[4];      // adj(M) (J z): phase numerator of h is sM * h . phw mod q
+  int symbol;
+  double eta;
+  long long K[16];       // sign(det M) J^T adj(M^T): N^{-T} h = K h / q
+  int K32[16];           // the same in int32 when `small`
+  int small;             // |K h| < 2^30 for every box point h: int32 arithmetic
+  int vpar[4];           // parity vector of J^T Z^d
+  FastDiv div2q;         // division by 2q (int32 path)
+  int off2q;             // multiple of 2q that makes K h non-negative (int32 path)
+  int ph32[4];           // sign(det M) adj(M) (J z) mod q (int32 path)
+  FastDiv divq;          // division by q (int32 path)
+  int offq;              // multiple of q that makes ph32 . h non-negative
+  const void* tab_lo;    // exp(-2 pi i t / q), t < 2^kLoBits
+  const void* tab_hi;    // exp(-2 pi i (t << kLoBits) / q)
+};
+
+// Periodised weight w(N^{-T} h) of the point h (see the header comment);
+// the fibre partner has weight 1 - w.
+template <typename Rl, bool SMALL>
+__device__ __forceinline__ Rl fibre_weight(const LevelDesc& L, const int* h) {
+  using I = typename std::conditional<SMALL, int, long long>::type;
+  const int d = L.d;
+  const I q = I(L.q);
+  Rl prod = Rl(1);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (j >= d) break;
+    I t;  // numerator of (N^{-T} h)_j mod 2, in [0, 2q)
+    if constexpr (SMALL) {
+      int acc = L.off2q;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < d) acc += L.K32[j * d + i] * h[i];
+      t = L.div2q.mod(acc);
+    } else {
+      long long acc = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < d) acc += L.K[j * d + i] * (long long)h[i];
+      t = acc % (2 * q);
+      if (t < 0) t += 2 * q;
+    }
+    Rl U = Rl(0);
+#pragma unroll
+    for (int n = 0; n >= -2; --n) {  // shifts with |t/q + n| possibly < 1
+      const I sn = t + I(n) * q;
+      const I an = sn < 0 ? -sn : sn;
+      Rl b;
+      if (L.symbol == PWT_DIRICHLET) {
+        b = (2 * an < q) ? Rl(1) : (2 * an == q) ? Rl(0.5) : Rl(0);
+      } else {
+        const Rl eta = Rl(L.eta);
+        b = (Rl(0.5) * (Rl(1) + eta) - Rl(an) / Rl(q)) / eta;
+        b = b < Rl(0) ? Rl(0) : (b > Rl(1) ? Rl(1) : b);
+      }
+      U += ((L.vpar[j] & n) & 1) ? -b : b;
+    }
+    prod *= U;
+  }
+  return Rl(0.5) * (Rl(1) + prod);
+}
+
+template <typename C, bool TAB = true, bool SMALL = false>
+__device__ __forceinline__ C wavelet_phase(const LevelDesc& L, const int* h) {
+  long long t = 0;
+  if constexpr (SMALL) {
+    int acc = L.offq;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i < L.d) acc += L.ph32[i] * h[i];
+    t = L.divq.mod(acc);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)  // each product < 2^62; reduce term by term
+      if (i < L.d) t += ((long long)h[i] * L.phw[i]) % L.q;
+    t = (L.sM * t) % L.q;
+    if (t < 0) t += L.q;
+  }
+  if constexpr (!TAB) {
+    // no tables: sincospi, in the working precision, of the exactly reduced
+    // fraction t / q
+    using Rl = decltype(C::x);
+    if constexpr (std::is_same<Rl, double>::value) {
+      double sn, cs;
+      sincospi(2.0 * (double(t) / double(L.q)), &sn, &cs);
+      return cmake<C>(cs, -sn);
+    } else {
+      float sn, cs;
+      sincospif(2.0f * (float(t) / float(L.q)), &sn, &cs);
+      return cmake<C>(cs, -sn);
+    }
+  }
+  const C* lo = static_cast<const C*>(L.tab_lo);
+  const C* hi = static_cast<const C*>(L.tab_hi);
+  return cmul(hi[t >> kLoBits], lo[t & ((1 << kLoBits) - 1)]);
+}
+
+// mode 0: decompose c -> (d1, d2); 1: reconstruct; 2: adjoint, for the
+// fibre of slot gs of the box of H(N^T).  The pointers address one signal.
+template <typename C, int MODE, bool TAB, bool SMALL>
+__device__ __forceinline__ void split_fibre(const LevelDesc& L, int gs, const C* __restrict__ cin,
+                                            C* __restrict__ cout, const C* __restrict__ d1in,
+                                            const C* __restrict__ d2in, C* __restrict__ d1out,
+                                            C* __restrict__ d2out) {
+  using Rl = decltype(C::x);
+  int g[4] = {0, 0, 0, 0}, h1[4] = {0, 0, 0, 0};
+  int s = gs;
+  for (int r = L.d - 1; r >= 0; --r) {
+    const int qd = L.divHN[r].div(s);
+    g[r] = s - qd * L.HNext[r];
+    s = qd;
+  }
+  int slot0 = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    if (r < L.d) {
+      h1[r] = g[r] + L.shift1[r];
+      slot0 += g[r] * L.HM.stride[r];
+    }
+  }
+  box_fix(L.HM, h1);
+  int slot1 = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    if (r < L.d) slot1 += h1[r] * L.HM.stride[r];
+  const Rl w0 = fibre_weight<Rl, SMALL>(L, g);
+  const Rl w1 = Rl(1) - w0;
+  Rl A0, A1;
+  if (L.symbol == PWT_DIRICHLET) {
+    A0 = sqrt(Rl(2) * w0);
+    A1 = sqrt(Rl(2) * w1);
+  } else {
+    A0 = Rl(1.41421356237309504880) * w0;
+    A1 = Rl(1.41421356237309504880) * w1;
+  }
+  // B(h0) = A(h1) e(h0), B(h1) = A(h0) e(h1), e(h1) = -e(h0)
+  const C e0 = wavelet_phase<C, TAB, SMALL>(L, g);
+  const Rl r2 = Rl(0.70710678118654752440);
+  if (MODE == 0) {
+    const C c0 = cin[slot0], c1 = cin[slot1];
+    d1out[gs] = cscale(cadd(cscale(c0, A0), cscale(c1, A1)), r2);
+    // conj(B0) c0 + conj(B1) c1 = conj(e0) (A1 c0 - A0 c1)
+    d2out[gs] = cscale(cmul(cconj(e0), csub(cscale(c0, A1), cscale(c1, A0))), r2);
+  } else {
+    const C a = d1in[gs], bb = d2in[gs];
+    const Rl S = A0 * A0 + A1 * A1;
+    const Rl fac = (MODE == 1) ? Rl(1.41421356237309504880) / S : r2;
+    const C eb = cmul(e0, bb);
+    cout[slot0] = cscale(cadd(cscale(a, A0), cscale(eb, A1)), fac);
+    cout[slot1] = cscale(csub(cscale(a, A1), cscale(eb, A0)), fac);
+  }
+}
+
+// One thread per fibre g (grid-stride over the slots of one signal,
+// blockIdx.y = signal).
+template <typename C, int MODE, bool TAB = true, bool SMALL = false>
+__global__ void __launch_bounds__(256) split_kernel(LevelDesc L, int batch, const C* __restrict__ cin,
+                                                    C* __restrict__ cout, const C* __restrict__ d1in,
+                                                    const C* __restrict__ d2in, C* __restrict__ d1out,
+                                                    C* __restrict__ d2out) {
+  (void)batch;
+  const long long oM = (long long)blockIdx.y * L.mM, oN = (long long)blockIdx.y * L.mN;
+  for (int gs = blockIdx.x * blockDim.x + threadIdx.x; gs < L.mN; gs += gridDim.x * blockDim.x)
+    split_fibre<C, MODE, TAB, SMALL>(L, gs, MODE == 0 ? cin + oM : nullptr, MODE == 0 ? nullptr : cout + oM,
+                                     MODE == 0 ? nullptr : d1in + oN, MODE == 0 ? nullptr : d2in + oN,
+                                     MODE == 0 ? d1out + oN : nullptr, MODE == 0 ? d2out + oN : nullptr);
+}
+
+// Host: the descriptor of one split level of M by J (wavelet.cu).
+pfft_status describe_split_level(int d, const int64_t* M, const int64_t* J, int symbol, double eta,
+                                 LevelDesc* out);
+
+}  // namespace pfft

@@ -26,7 +26,7 @@ WORKLOADS = {
     "batched_2d": dict(M=M_BATCHED_2D, batch=8, seed=1),
     "autograd_3d": dict(M=M_AUTOGRAD_3D, batch=4, seed=2),
     "wavelet_2d": dict(M=M_WAVELET_2D, batch=16, seed=3, levels=12),
-    "uneven_mix": dict(n_patterns=4096, seed=4),
+    "uneven_mix": dict(n_patterns=4096, seed=4, even_det=True),
 }
 
 SAMPLE_SEED = 12345
@@ -43,6 +43,14 @@ def complex_normal(batch: int, n: int, seed: int, dtype=np.complex64) -> np.ndar
     re = rng.standard_normal((batch, n))
     im = rng.standard_normal((batch, n))
     return (re + 1j * im).astype(dtype)
+
+
+def complex_normal_flat(n: int, seed: int) -> np.ndarray:
+    """[n] complex64 values, real and imaginary parts i.i.d. N(0,1), drawn in
+    single precision (interleaved re, im) -- the concatenated signals of a
+    pattern batch."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(2 * n, dtype=np.float32).view(np.complex64)
 
 
 def uniform01(shape, seed: int, dtype=np.float64) -> np.ndarray:
@@ -71,10 +79,11 @@ def random_upper_triangular(rng, d: int, lo: int, hi: int):
 
 
 def uneven_mix(n_patterns: int = 4096, seed: int = 4, max_det: int = 1 << 20,
-               lo: int = 16, hi: int = 512):
+               lo: int = 16, hi: int = 512, even_det: bool = False):
     """Patterns of the uneven serving-style mix: d uniform in {2, 3}, upper
     triangular, diagonals uniform in [lo, hi], off-diagonals in [0, diag),
-    resampled until the determinant (product of the diagonal) is <= max_det."""
+    resampled until the determinant (product of the diagonal) is <= max_det
+    (and even, if ``even_det``: a dilation of determinant 2 needs it)."""
     rng = np.random.default_rng(seed)
     out = []
     while len(out) < n_patterns:
@@ -83,9 +92,45 @@ def uneven_mix(n_patterns: int = 4096, seed: int = 4, max_det: int = 1 << 20,
         prod = 1
         for r in range(d):
             prod *= M[r][r]
-        if prod <= max_det:
+        if prod <= max_det and (prod % 2 == 0 or not even_det):
             out.append(M)
     return out
+
+
+def parity_dilation(M):
+    """A dilation J with |det J| = 2 and J^{-1} M integral, for an integer
+    matrix M of even determinant (workload construction, not part of the
+    method).  J Z^d = {x : v . x even} for a non-zero v in {0,1}^d with
+    v^T M = 0 mod 2 (one exists: M mod 2 is singular).  With r the last index
+    where v_r = 1, the columns e_j - v_j e_r (j != r) and 2 e_r span that
+    lattice: J = I + e_r w^T, w_j = -v_j (j != r), w_r = 1."""
+    d = len(M)
+    A = [[int(M[i][j]) & 1 for i in range(d)] for j in range(d)]  # rows of M^T mod 2
+    # null vector of M^T over GF(2) by elimination (d <= 4: plain loops)
+    piv_cols, rows = [], [r[:] for r in A]
+    rank = 0
+    for c in range(d):
+        p = next((r for r in range(rank, d) if rows[r][c]), None)
+        if p is None:
+            continue
+        rows[rank], rows[p] = rows[p], rows[rank]
+        for r in range(d):
+            if r != rank and rows[r][c]:
+                rows[r] = [a ^ b for a, b in zip(rows[r], rows[rank])]
+        piv_cols.append(c)
+        rank += 1
+    free = [c for c in range(d) if c not in piv_cols]
+    if not free:
+        raise ValueError("det M is odd: no dilation of determinant 2 divides M")
+    v = [0] * d
+    v[free[0]] = 1
+    for i, c in enumerate(piv_cols):
+        v[c] = rows[i][free[0]]
+    r = max(i for i in range(d) if v[i])
+    J = [[int(i == j) for j in range(d)] for i in range(d)]
+    for j in range(d):
+        J[r][j] = 2 if j == r else -v[j]
+    return J
 
 
 def random_regular_matrix(rng, d: int, amax: int, max_det: int):

@@ -36,6 +36,11 @@ SMALL = [
     [[4, 1], [0, 8192]],                    # one cycle of 32768: split four-step (2 x 16384)
     [[17, 0], [0, 2048]],                   # one cycle of 34816 = 17 * 2^11: split, mixed radix
     [[2, 1, 0], [0, 2, 1], [0, 0, 8192]],   # one cycle of 32768 in d = 3
+    [[37, 0], [0, 41]],                     # cyclic 1517: two direct prime stages, the second twiddled
+    [[74, 0], [0, 148]],                    # (74, 148): direct radix 37 in both passes
+    [[11, 3, 5], [0, 13, 2], [0, 0, 4]],    # 572 = 4 * 11 * 13 in d = 3
+    [[509, 0], [0, 67]],                    # cyclic 34103 = 509 * 67: split, direct stages in both passes
+    [[23, 7], [0, 46]],                     # (23, 46): odd column tile count
 ]
 
 
@@ -209,3 +214,21 @@ def test_long_cycle_fp64_full():
     y = plan.forward(_gpu(c)).cpu().numpy()
     assert rel_l2(y, oracle.pattern_fft(M, c)) <= 1e-12
     assert rel_l2(plan.inverse(_gpu(y)).cpu().numpy(), c) <= 1e-12
+
+
+def test_largest_direct_primes_sampled():
+    """One cycle of 1021 * 1019 (the largest supported prime radices), split
+    four-step; 512 sampled frequencies and the round trip."""
+    M = [[1021, 0], [0, 1019]]
+    plan = pf.PatternFFT(M, 1)
+    c = SI.complex_normal(1, plan.m, 31)
+    y = plan.forward(_gpu(c)).cpu().numpy()
+    slots = SI.sample_slots(plan.m, 512, seed=3)
+    assert rel_l2(y[:, slots], oracle.pattern_fft(M, c, out_slots=slots)) <= 1e-5
+    assert rel_l2(plan.inverse(_gpu(y)).cpu().numpy(), c) <= 1e-5
+
+
+def test_prime_beyond_direct_limit_is_rejected():
+    with pytest.raises(pf.PfftError) as e:
+        pf.PatternFFT([[1031, 0], [0, 2]], 1)
+    assert e.value.status == 5

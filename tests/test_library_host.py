@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_1107_5415_gb300 as pf
 from paper_1107_5415_gb300 import _capi
 from oracle import lattice as L
@@ -95,6 +96,45 @@ def test_plan_without_gpu_fails_loudly():
     assert e.value.status == 7  # PFFT_ERR_CUDA: no CPU fallback
     with pytest.raises(pf.PfftError):
         pf.WaveletSplit(SI.M_WAVELET_2D, SI.wavelet_dilations(2))
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU path")
+def test_batch_without_gpu_fails_loudly():
+    with pytest.raises(pf.PfftError) as e:
+        pf.PatternBatch([SI.M_SMALL_2D, [[4, 1], [0, 6]]])
+    assert e.value.status == 7
+
+
+def test_batch_argument_errors():
+    with pytest.raises(pf.PfftError) as e:
+        pf.pfft_batch_create([2 * np.eye(5, dtype=np.int64)])
+    assert e.value.status == 1  # d = 5
+    with pytest.raises(pf.PfftError) as e:
+        pf.pfft_batch_create([[[2, 0], [0, 2]]], [[[2, 0], [0, 1]]], symbol=7)
+    assert e.value.status == 1  # unknown symbol
+    with pytest.raises(pf.PfftError) as e:
+        pf.pfft_batch_create([[[2, 0], [0, 2]]], [[[2, 0], [0, 1]]], symbol=pf.PWT_DLVP, eta=1.5)
+    assert e.value.status == 1  # blend width outside (0, 1)
+    with pytest.raises(ValueError):
+        pf.pfft_batch_create([[[2, 0], [0, 2]]], [[[2, 0], [0, 1]], [[2, 0], [0, 1]]])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_parity_dilation_divides_pattern(seed):
+    """The workload helper that picks a dilation for each pattern of the
+    uneven mix: |det J| = 2 and J^{-1} M integral, for triangular and general
+    matrices of even determinant; odd determinants are refused."""
+    rng = np.random.default_rng(seed)
+    for _ in range(40):
+        d = int(rng.integers(1, 5))
+        M = SI.random_regular_matrix(rng, d, 9, 1 << 16)
+        if L.det(M) % 2:
+            with pytest.raises(ValueError):
+                SI.parity_dilation(M)
+            continue
+        J = SI.parity_dilation(M)
+        assert abs(L.det(J)) == 2
+        oracle.exact_N(M, J)  # raises unless J^{-1} M is integral
 
 
 def test_plan_argument_errors():
