@@ -104,11 +104,16 @@ void make_buckets(std::vector<Item>& items, int cols, int order, std::vector<Buc
     Bucket b;
     b.cols = cols;
     b.n = int(v.size());
+    int tmax = 1;
     for (auto& it : v) {
       b.nctas += it.a.groups;
       b.threads = std::max(b.threads, it.a.nthreads);
       b.smem = std::max(b.smem, it.a.smem_bytes);
+      tmax = std::max(tmax, it.a.T);
     }
+    // a column pass keeps one column per thread: the block size must be a
+    // multiple of every item's T (powers of two up to 512)
+    if (cols && b.threads % tmax) b.threads = (b.threads + tmax - 1) / tmax * tmax;
     out.push_back(b);
     groups.push_back(std::move(v));
   }
@@ -190,7 +195,8 @@ pfft_status build_schedule(pfft_batch_s& B) {
     std::vector<int> c0(1, 0);
     for (int i : sorder) {
       si.push_back(B.sitems[i]);
-      c0.push_back(c0.back() + int((B.sitems[i].L.mN + kSplitThreads - 1) / kSplitThreads));
+      const int per_cta = kSplitThreads * kSplitPerThread;
+      c0.push_back(c0.back() + int((B.sitems[i].L.mN + per_cta - 1) / per_cta));
     }
     Bucket b;
     b.n = int(si.size());

@@ -9,6 +9,7 @@
 namespace pfft {
 
 constexpr int kSplitThreads = 256;
+constexpr int kSplitPerThread = 4;  // fibres per thread of a grouped split CTA
 // Dynamic shared memory of a grouped pass CTA: the 227 KB per CTA less room
 // for the static copy of its pass descriptor.
 constexpr int kGroupedMaxDynSmem = 227 * 1024 - 4096;

@@ -45,10 +45,18 @@ __global__ void __launch_bounds__(kMaxThreads, 1) grouped_pass_kernel(GroupArgs 
   }
   __syncthreads();
   const int tile = blockIdx.x - __ldg(g.cta0 + it);
-  if constexpr (COLS)
-    col_pass_body<C, EPT, false>(a, tile, 0, reinterpret_cast<C*>(smem_raw));
-  else
-    row_pass_body<C, EPT, false>(a, tile, 0, reinterpret_cast<C*>(smem_raw));
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  if constexpr (COLS) {
+    if (a.pad)
+      col_pass_body<C, EPT, false, true>(a, tile, 0, sm);
+    else
+      col_pass_body<C, EPT, false, false>(a, tile, 0, sm);
+  } else {
+    if (a.pad)
+      row_pass_body<C, EPT, false, true>(a, tile, 0, sm);
+    else
+      row_pass_body<C, EPT, false, false>(a, tile, 0, sm);
+  }
 }
 
 template <typename C>
@@ -60,15 +68,19 @@ __global__ void __launch_bounds__(kSplitThreads) grouped_split_kernel(const Spli
   const int k = find_item(cta0, n, blockIdx.x);
   copy_to_smem(&it, items + k);
   __syncthreads();
-  const int gs = (blockIdx.x - __ldg(cta0 + k)) * blockDim.x + threadIdx.x;
-  if (gs >= it.L.mN) return;
+  const int g0 = (blockIdx.x - __ldg(cta0 + k)) * (kSplitThreads * kSplitPerThread) + threadIdx.x;
   const C* cin = chat + it.in_off;
   C* d1 = sc + it.out_off;
   C* d2 = wv + it.out_off;
-  if (it.L.small)
-    split_fibre<C, 0, false, true>(it.L, gs, cin, nullptr, nullptr, nullptr, d1, d2);
-  else
-    split_fibre<C, 0, false, false>(it.L, gs, cin, nullptr, nullptr, nullptr, d1, d2);
+#pragma unroll
+  for (int f = 0; f < kSplitPerThread; ++f) {
+    const int gs = g0 + f * kSplitThreads;
+    if (gs >= it.L.mN) break;
+    if (it.L.small)
+      split_fibre<C, 0, false, true>(it.L, gs, cin, nullptr, nullptr, nullptr, d1, d2);
+    else
+      split_fibre<C, 0, false, false>(it.L, gs, cin, nullptr, nullptr, nullptr, d1, d2);
+  }
 }
 
 namespace {

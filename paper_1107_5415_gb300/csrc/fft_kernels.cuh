@@ -11,8 +11,12 @@
 namespace pfft {
 
 // Shared-memory index with one padding element per 16, which keeps the
-// stride-R writes of the first radix stages free of bank conflicts.
-__device__ __forceinline__ int phys(int x) { return x + (x >> 4); }
+// stride-R writes of the first radix stages free of bank conflicts.  Passes
+// with direct prime stages run unpadded (PAD = false): those stages read
+// consecutive addresses across a warp anyway and walk their inputs with
+// pointer increments.
+template <bool PAD>
+__device__ __forceinline__ int phys(int x) { return PAD ? x + (x >> 4) : x; }
 
 // Multiply v[r] by w^r, w = tw[base], r = 1..R-1.  The powers w^(2^b) come
 // from the table and w^r is their product over the set bits of r, so every
@@ -42,7 +46,7 @@ __device__ __forceinline__ void apply_twiddles(C* v, const C* __restrict__ tw, i
 // pass).  Butterfly j of the axis reads i = base + (j + r a/R) sigma and,
 // after the twiddles exp(-2 pi i k r / (Ns R)) (k = j mod Ns) and the
 // length-R DFT, writes i = base + ((j - k) R + k + r Ns) sigma.
-template <typename C, int R, int NB, bool COLS>
+template <typename C, int R, int NB, bool COLS, bool PAD>
 __device__ __forceinline__ void run_stage(C* sm, const PassArgs& a, const StageDesc& s,
                                           const C* __restrict__ tw) {
   const int per_pencil = a.L / R;
@@ -71,7 +75,7 @@ __device__ __forceinline__ void run_stage(C* sm, const PassArgs& a, const StageD
       const int k = j - s.div_Ns.div(j) * s.Ns;
       const int ebase = COLS ? base * a.T + t : t * a.L + base;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = sm[phys(ebase + (j + r * s.aR) * s.sigma * escale)];
+      for (int r = 0; r < R; ++r) v[q][r] = sm[phys<PAD>(ebase + (j + r * s.aR) * s.sigma * escale)];
       if (s.Ns > 1) apply_twiddles<C, R>(v[q], tw, k * s.twstep);
       obase[q] = ebase + ((j - k) * R + k) * s.sigma * escale;
     }
@@ -82,31 +86,37 @@ __device__ __forceinline__ void run_stage(C* sm, const PassArgs& a, const StageD
     if (obase[q] >= 0) {
       dft<C, R>(v[q], tw, a.tw_n);
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[phys(obase[q] + r * ostep)] = v[q][r];
+      for (int r = 0; r < R; ++r) sm[phys<PAD>(obase[q] + r * ostep)] = v[q][r];
     }
   }
   __syncthreads();
 }
 
-// One stage of a prime radix R >= 11, evaluated directly: with
-// x'_r = x_r exp(-2 pi i r k / (Ns R)) (k = j mod Ns, applied in place first
-// when Ns > 1), output s of butterfly j is sum_r x'_r omega_R^(r s).  Outputs
-// s and R - s share the products (their twiddles are conjugate), so one work
-// item accumulates four real sums for the pair.  Lanes of a warp take
-// consecutive butterflies of the same output pair: the x reads are
-// consecutive and the omega_R reads (a table of R entries after the tile) are
-// broadcasts.  Every read of the stage happens before its first write.
-template <typename C, int NBI, bool COLS>
+// One stage of a prime radix R >= 11, evaluated directly.  With
+// x'_r = x_r exp(-2 pi i r k / (Ns R)) (k = j mod Ns; no twiddle when Ns = 1)
+// and h = (R - 1) / 2, a pre-pass forms, in place,
+//     a_r = x'_r + x'_{R-r}  (slot r),   b_r = x'_r - x'_{R-r}  (slot R - r),   r = 1..h,
+// and since omega_R^{(R-r) s} = conj(omega_R^{r s}), outputs s and R - s are
+//     y_s     = x_0 + sum_{r=1..h} (a_r c_rs - i b_r s_rs),
+//     y_{R-s} = x_0 + sum_{r=1..h} (a_r c_rs + i b_r s_rs),
+// c_rs - i s_rs = omega_R^{r s}: one work item accumulates the four real sums
+// of the pair in h steps.  Lanes of a warp take consecutive butterflies of
+// the same output pair, so the a, b reads are consecutive and the omega_R
+// reads (a table of R entries after the tile) are broadcasts.  Every read of
+// the stage happens before its first write.
+template <typename C, int NBI, bool COLS, bool PAD>
 __device__ __noinline__ void run_direct_stage(C* sm, const PassArgs& a, const StageDesc& s,
                                               const C* __restrict__ tw) {
   using Rl = decltype(C::x);
   const int R = s.R;
+  const int h = (R - 1) / 2;
   const int per_pencil = a.L / R;
   const int nbfly = a.T * per_pencil;
   const int npair = (R + 1) / 2;
   const int nthr = blockDim.x;
   const int escale = COLS ? a.T : 1;
   const int step = s.sigma * escale;
+  const int istep = s.aR * step;  // element distance of consecutive inputs r
   C* W = sm + a.dir_off;
   const int wstride = a.tw_n / R;
   for (int e = threadIdx.x; e < R; e += nthr) W[e] = __ldg(tw + e * wstride);
@@ -126,19 +136,23 @@ __device__ __noinline__ void run_direct_stage(C* sm, const PassArgs& a, const St
     k = j - s.div_Ns.div(j) * s.Ns;
     ebase = COLS ? base * a.T + t : t * a.L + base;
   };
-  if (s.Ns > 1) {  // x_r *= exp(-2 pi i r k / (Ns R)), in place (one owner per element)
-    const int NsR = s.Ns * R;
-    for (int w = threadIdx.x; w < nbfly * R; w += nthr) {
-      const int r = w / nbfly;
-      const int b = w - r * nbfly;
-      int ebase, k, j;
-      locate(b, ebase, k, j);
-      const int idx = int((int64_t(r) * k) % NsR);
-      if (idx) {
-        C* x = sm + phys(ebase + (j + r * s.aR) * step);
-        *x = cmul(*x, __ldg(tw + idx * s.twstep));
-      }
+  // pre-pass: twiddles and the symmetric / antisymmetric combinations
+  const int NsR = s.Ns * R;
+  for (int w = threadIdx.x; w < nbfly * h; w += nthr) {
+    const int r = w / nbfly + 1;
+    const int b = w - (r - 1) * nbfly;
+    int ebase, k, j;
+    locate(b, ebase, k, j);
+    C* p0 = sm + phys<PAD>(ebase + j * step + r * istep);
+    C* p1 = sm + phys<PAD>(ebase + j * step + (R - r) * istep);
+    C u = *p0, v = *p1;
+    if (s.Ns > 1) {
+      const int i0 = int((int64_t(r) * k) % NsR), i1 = int((int64_t(R - r) * k) % NsR);
+      u = cmul(u, __ldg(tw + i0 * s.twstep));
+      v = cmul(v, __ldg(tw + i1 * s.twstep));
     }
+    *p0 = cadd(u, v);
+    *p1 = csub(u, v);
   }
   __syncthreads();
   C y0[NBI], y1[NBI];
@@ -152,24 +166,41 @@ __device__ __noinline__ void run_direct_stage(C* sm, const PassArgs& a, const St
       const int b = w - q * nbfly;
       int ebase, k, j;
       locate(b, ebase, k, j);
-      const C* x = sm;
       const int i0 = ebase + j * step;
-      const int istep = s.aR * step;
-      Rl A = 0, B = 0, Cs = 0, Ds = 0;
+      const C x0 = sm[phys<PAD>(i0)];
+      Rl P1 = x0.x, P3 = x0.y, P2 = 0, P4 = 0;
       int idx = 0;
+      if constexpr (PAD) {
 #pragma unroll 4
-      for (int r = 0; r < R; ++r) {
-        const C xv = x[phys(i0 + r * istep)];
-        const C wv = W[idx];
-        A = fma(xv.x, wv.x, A);
-        B = fma(xv.y, wv.y, B);
-        Cs = fma(xv.x, wv.y, Cs);
-        Ds = fma(xv.y, wv.x, Ds);
-        idx += q;
-        if (idx >= R) idx -= R;
+        for (int r = 1; r <= h; ++r) {
+          idx += q;
+          if (idx >= R) idx -= R;
+          const C av = sm[phys<PAD>(i0 + r * istep)];
+          const C bv = sm[phys<PAD>(i0 + (R - r) * istep)];
+          const C wv = W[idx];  // (c, -s)
+          P1 = fma(av.x, wv.x, P1);
+          P2 = fma(bv.y, wv.y, P2);  // -sum b.im s
+          P3 = fma(av.y, wv.x, P3);
+          P4 = fma(bv.x, wv.y, P4);  // -sum b.re s
+        }
+      } else {
+        const C* pa = sm + i0 + istep;
+        const C* pb = sm + i0 + (R - 1) * istep;
+#pragma unroll 4
+        for (int r = 1; r <= h; ++r) {
+          idx += q;
+          if (idx >= R) idx -= R;
+          const C av = *pa, bv = *pb, wv = W[idx];
+          pa += istep;
+          pb -= istep;
+          P1 = fma(av.x, wv.x, P1);
+          P2 = fma(bv.y, wv.y, P2);
+          P3 = fma(av.y, wv.x, P3);
+          P4 = fma(bv.x, wv.y, P4);
+        }
       }
-      y0[u] = cmake<C>(A - B, Cs + Ds);  // output q
-      y1[u] = cmake<C>(A + B, Ds - Cs);  // output R - q
+      y0[u] = cmake<C>(P1 - P2, P3 + P4);  // output q
+      y1[u] = cmake<C>(P1 + P2, P3 - P4);  // output R - q
       ob[u] = ebase + ((j - k) * R + k) * step;
       qs[u] = q;
     }
@@ -179,8 +210,8 @@ __device__ __noinline__ void run_direct_stage(C* sm, const PassArgs& a, const St
 #pragma unroll
   for (int u = 0; u < NBI; ++u) {
     if (ob[u] >= 0) {
-      sm[phys(ob[u] + qs[u] * ostep)] = y0[u];
-      if (qs[u] > 0) sm[phys(ob[u] + (R - qs[u]) * ostep)] = y1[u];
+      sm[phys<PAD>(ob[u] + qs[u] * ostep)] = y0[u];
+      if (qs[u] > 0) sm[phys<PAD>(ob[u] + (R - qs[u]) * ostep)] = y1[u];
     }
   }
   __syncthreads();
@@ -192,16 +223,16 @@ __device__ __noinline__ void run_direct_stage(C* sm, const PassArgs& a, const St
 // register allocation of each butterfly size separate (mixing sizes inside
 // one loop body makes the allocator spill).  POW2 kernels carry only the
 // power-of-two regions.
-template <typename C, int EPT, bool COLS, bool POW2>
+template <typename C, int EPT, bool COLS, bool POW2, bool PAD>
 __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ tw) {
   int i = 0;
   if constexpr (!POW2) {
     _Pragma("unroll 1") for (int q = 0; q < a.cnt[kDirectRegion]; ++q, ++i)
-        run_direct_stage<C, kDirectItems<EPT>, COLS>(sm, a, a.st[i], tw);
+        run_direct_stage<C, kDirectItems<EPT>, COLS, PAD>(sm, a, a.st[i], tw);
   }
 #define PFFT_REGION(RR, IDX)                                                     \
   _Pragma("unroll 1") for (int q = 0; q < a.cnt[IDX]; ++q, ++i)                  \
-      run_stage<C, RR, (EPT / RR > 0 ? EPT / RR : 1), COLS>(sm, a, a.st[i], tw);
+      run_stage<C, RR, (EPT / RR > 0 ? EPT / RR : 1), COLS, PAD>(sm, a, a.st[i], tw);
   PFFT_REGION(16, 0)
   PFFT_REGION(8, 1)
   PFFT_REGION(4, 2)
@@ -223,7 +254,7 @@ __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ t
 // The body takes the tile (blockIdx.x of a plain launch) and the signal index
 // (blockIdx.y) as arguments so that the grouped launches of many patterns
 // (batch_kernels.cu) run the same code on a per-CTA copy of the arguments.
-template <typename C, int EPT, bool POW2>
+template <typename C, int EPT, bool POW2, bool PAD>
 __device__ __forceinline__ void row_pass_body(const PassArgs& a, int tile, int sig, C* sm) {
   const C* __restrict__ tw = static_cast<const C*>(a.tw);
   const C* __restrict__ in = static_cast<const C*>(a.in) + (int64_t)sig * a.m;
@@ -265,10 +296,10 @@ __device__ __forceinline__ void row_pass_body(const PassArgs& a, int tile, int s
   }
 #pragma unroll
   for (int k = 0; k < CH; ++k)
-    if (sidx[k] >= 0) sm[phys(sidx[k])] = (a.load_mode == MAP_WS) ? v[k] : maybe_conj(v[k], a.conj_in);
+    if (sidx[k] >= 0) sm[phys<PAD>(sidx[k])] = (a.load_mode == MAP_WS) ? v[k] : maybe_conj(v[k], a.conj_in);
   }
   __syncthreads();
-  run_all_stages<C, EPT, false, POW2>(sm, a, tw);
+  run_all_stages<C, EPT, false, POW2, PAD>(sm, a, tw);
   using Rl = decltype(C::x);
   const Rl sc = Rl(a.scale);
 #pragma unroll
@@ -286,14 +317,14 @@ __device__ __forceinline__ void row_pass_body(const PassArgs& a, int tile, int s
       if (row < a.LB) {
         if (a.store_mode == MAP_WS) {
           const int mu = __ldg(a.PIinv + e);
-          v[k] = sm[phys(t * a.nD + mu)];
+          v[k] = sm[phys<PAD>(t * a.nD + mu)];
           if (a.fs_na > 1) v[k] = cmul(v[k], fs_twiddle<C>(a, row, mu));
           gidx[k] = row * a.nD + e;
         } else if (a.store_mode == MAP_BOX_H) {
-          v[k] = cscale(maybe_conj(sm[phys(t * a.nD + e)], a.conj_out), sc);
+          v[k] = cscale(maybe_conj(sm[phys<PAD>(t * a.nD + e)], a.conj_out), sc);
           gidx[k] = box_sum_slot(a.boxH, a.Atab + row * a.ts, a.Btab + e * a.ts);
         } else {
-          v[k] = cscale(maybe_conj(sm[phys(t * a.nD + __ldg(a.PIinv + e))], a.conj_out), sc);
+          v[k] = cscale(maybe_conj(sm[phys<PAD>(t * a.nD + __ldg(a.PIinv + e))], a.conj_out), sc);
           gidx[k] = box_sum_slot(a.boxG, a.Ctab + row * a.ts, a.Etab + e * a.ts);
         }
       }
@@ -328,7 +359,7 @@ __device__ __forceinline__ int shear_index(const PassArgs& a, int j, const int* 
 // Column pass: all LB rows of T adjacent workspace columns per CTA, smem
 // layout [i][t].  The DFT runs over the (D-1) cycles inside the pencil.
 // Loads and stores are batched per thread as in the row pass.
-template <typename C, int EPT, bool POW2>
+template <typename C, int EPT, bool POW2, bool PAD>
 __device__ __forceinline__ void col_pass_body(const PassArgs& a, int tile, int sig, C* sm) {
   const C* __restrict__ tw = static_cast<const C*>(a.tw);
   const C* __restrict__ in = static_cast<const C*>(a.in) + (int64_t)sig * a.m;
@@ -373,10 +404,10 @@ __device__ __forceinline__ void col_pass_body(const PassArgs& a, int tile, int s
   }
 #pragma unroll
   for (int k = 0; k < CH; ++k)
-    if (sidx[k] >= 0) sm[phys(sidx[k])] = maybe_conj(v[k], a.conj_in);
+    if (sidx[k] >= 0) sm[phys<PAD>(sidx[k])] = maybe_conj(v[k], a.conj_in);
   }
   __syncthreads();
-  run_all_stages<C, EPT, true, POW2>(sm, a, tw);
+  run_all_stages<C, EPT, true, POW2, PAD>(sm, a, tw);
   using Rl = decltype(C::x);
   const Rl sc = Rl(a.scale);
   const bool ws_out = a.store_mode == MAP_WS;
@@ -391,11 +422,11 @@ __device__ __forceinline__ void col_pass_body(const PassArgs& a, int tile, int s
     if (w < n_ok) {
       const int j = a.divT.div(w);
       if (ws_out) {
-        v[k] = sm[phys(j * a.T + tcol)];
+        v[k] = sm[phys<PAD>(j * a.T + tcol)];
         gidx[k] = j * a.nD + p0 + tcol;
       } else {
         const int i = shear_index(a, j, off);
-        v[k] = cscale(maybe_conj(sm[phys(i * a.T + tcol)], a.conj_out), sc);
+        v[k] = cscale(maybe_conj(sm[phys<PAD>(i * a.T + tcol)], a.conj_out), sc);
         gidx[k] = box_sum_slot(a.boxG, a.Ctab + i * a.ts, et);
       }
     }
@@ -406,16 +437,16 @@ __device__ __forceinline__ void col_pass_body(const PassArgs& a, int tile, int s
   }
 }
 
-template <typename C, int EPT, bool POW2>
+template <typename C, int EPT, bool POW2, bool PAD>
 __global__ void __launch_bounds__(kMaxThreads, 1) row_pass_kernel(PassArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  row_pass_body<C, EPT, POW2>(a, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
+  row_pass_body<C, EPT, POW2, PAD>(a, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
 }
 
-template <typename C, int EPT, bool POW2>
+template <typename C, int EPT, bool POW2, bool PAD>
 __global__ void __launch_bounds__(kMaxThreads, 1) col_pass_kernel(PassArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  col_pass_body<C, EPT, POW2>(a, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
+  col_pass_body<C, EPT, POW2, PAD>(a, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
 }
 
 // Allow the largest dynamic shared-memory size and prefer the maximum shared
@@ -427,17 +458,23 @@ inline int configure_kernel(const void* k) {
   return 0;
 }
 
-template <typename C, int EPT, bool POW2>
-inline int launch_typed(const PassArgs& a, cudaStream_t s) {
+template <typename C, int EPT, bool POW2, bool PAD>
+inline int launch_typed_pad(const PassArgs& a, cudaStream_t s) {
   dim3 grid(a.groups, a.batch), block(a.nthreads);
-  static const int row_ok = configure_kernel(reinterpret_cast<const void*>(row_pass_kernel<C, EPT, POW2>));
-  static const int col_ok = configure_kernel(reinterpret_cast<const void*>(col_pass_kernel<C, EPT, POW2>));
+  static const int row_ok = configure_kernel(reinterpret_cast<const void*>(row_pass_kernel<C, EPT, POW2, PAD>));
+  static const int col_ok = configure_kernel(reinterpret_cast<const void*>(col_pass_kernel<C, EPT, POW2, PAD>));
   if (row_ok != 0 || col_ok != 0) return -1;
   if (a.cols)
-    col_pass_kernel<C, EPT, POW2><<<grid, block, a.smem_bytes, s>>>(a);
+    col_pass_kernel<C, EPT, POW2, PAD><<<grid, block, a.smem_bytes, s>>>(a);
   else
-    row_pass_kernel<C, EPT, POW2><<<grid, block, a.smem_bytes, s>>>(a);
+    row_pass_kernel<C, EPT, POW2, PAD><<<grid, block, a.smem_bytes, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename C, int EPT, bool POW2>
+inline int launch_typed(const PassArgs& a, cudaStream_t s) {
+  if constexpr (POW2) return launch_typed_pad<C, EPT, true, true>(a, s);  // no direct stages
+  return a.pad ? launch_typed_pad<C, EPT, POW2, true>(a, s) : launch_typed_pad<C, EPT, POW2, false>(a, s);
 }
 
 }  // namespace pfft

@@ -223,12 +223,14 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
     }
   }
   p.nthreads = threads_for(p, ept);
+  if (cols && T > 32) p.nthreads = (p.nthreads + T - 1) / T * T;  // each thread keeps one column
   if (p.nthreads > kMaxThreads) return PFFT_ERR_UNSUPPORTED;
   const int nel = T * p.L;
   int rmax = 0;  // omega_R table of the direct stages, after the tile
   for (int i = 0; i < p.nstages; ++i)
     if (radix_region(p.st[i].R) == kDirectRegion) rmax = std::max(rmax, p.st[i].R);
-  p.dir_off = (nel - 1) + ((nel - 1) >> 4) + 1;
+  p.pad = rmax ? 0 : 1;
+  p.dir_off = p.pad ? (nel - 1) + ((nel - 1) >> 4) + 1 : nel;
   p.smem_bytes = int(size_t(p.dir_off + rmax) * elem_bytes(P.dtype));
   if (p.smem_bytes > 227 * 1024) return PFFT_ERR_UNSUPPORTED;
   return PFFT_OK;
@@ -595,7 +597,8 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
   pfft_status st = choose_and_configure(P.rowp, P, false, 64, std::max(budget, nD));
   if (st != PFFT_OK) return st;
   if (npen >= 1) {
-    st = choose_and_configure(P.colp, P, true, 16, std::max(budget, LB));
+    // generic column tiles may hold many short columns (split last cycles)
+    st = choose_and_configure(P.colp, P, true, P.generic_only ? 512 : 16, std::max(budget, LB));
     if (st != PFFT_OK) return st;
   }
   // stage twiddle tables of the register-resident passes, gathered on the
@@ -684,7 +687,7 @@ pfft_status pfft::plan_retile(pfft_plan_s& P, int row_budget, int col_budget) {
   if (!P.generic_only || P.D == 0) return PFFT_ERR_ARG;
   pfft_status st = choose_and_configure(P.rowp, P, false, 64, std::max(row_budget, P.nD));
   if (st != PFFT_OK || P.pen.empty()) return st;
-  return choose_and_configure(P.colp, P, true, 16, std::max(col_budget, P.LB));
+  return choose_and_configure(P.colp, P, true, 512, std::max(col_budget, P.LB));
 }
 
 void pfft::plan_release(pfft_plan_s* P) {

@@ -65,6 +65,7 @@ struct alignas(16) PassArgs {
   int nstages;
   int cnt[8];  // stages per radix, in the order of kRadixOrder; [7]: direct prime stages
   int dir_off;  // shared-memory element offset of the omega_R table of a direct stage
+  int pad;      // 1: padded shared-memory tile (x + x / 16); 0 when the pass has direct stages
   int pow2;     // all radices are powers of two
   int fast;       // 1: use the register-resident power-of-two kernels (fft_fast.cuh)
   int fast_tail;  // radix of the first stage (1 = none)
