@@ -235,6 +235,47 @@ def bench_wavelet(pf, torch, peaks_hbm, steps=20, warmup=3):
     return out
 
 
+def bench_tc(pf, torch, x, y_fp32, ms_fp32, peaks_hbm, steps=50, warmup=5):
+    """The same step (forward + inverse of the batched 2-D workload) in the
+    split-precision tensor-core form: radix-16 / 32 stages as fp16 hi + lo
+    DFT-matrix products on the tensor cores with fp32 accumulation.  Reports
+    its speed against the plain fp32 form measured above and its agreement
+    with it (the error against the FP64 oracle is checked by the tests)."""
+    w = SI.WORKLOADS[WORKLOAD]
+    plan = pf.PatternFFT(w["M"], x.shape[0], tc_split=True)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.forward(x, y)
+        plan.inverse(y, z)
+    torch.cuda.synchronize()
+    plan.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.forward(x, y)
+        plan.inverse(y, z)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof = plan.profile_read()
+    plan.close()
+    pts = 2.0 * x.numel()
+    num = torch.linalg.vector_norm((y - y_fp32).flatten()).item()
+    den = torch.linalg.vector_norm(y_fp32.flatten()).item()
+    rt = (torch.linalg.vector_norm((z - x).flatten()) / torch.linalg.vector_norm(x.flatten())).item()
+    kernels = {k: {"launches": int(v[0]), "avg_ms": v[1] / max(v[0], 1),
+                   "achieved_gbs": BYTES_PER_POINT_PASS * x.numel() / (v[1] / max(v[0], 1) * 1e-3) / 1e9}
+               for k, v in prof.items() if v[0]}
+    return {"form": "split fp16 (hi + lo) tensor-core radix-16/32 stages, fp32 accumulation",
+            "value": pts / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
+            "speedup_vs_plain_fp32": ms_fp32 / ms, "rel_l2_vs_plain_fp32": num / den,
+            "round_trip_rel_l2": rt, "kernels": kernels,
+            "compulsory_frac": BYTES_PER_POINT_PASS * pts / (ms * 1e-3) / 1e9 / peaks_hbm}
+
+
 def bench_mix(pf, torch, peaks_hbm, steps=10, warmup=3):
     """Uneven serving-style mix: 4096 seeded patterns (d in {2, 3}, upper
     triangular, diagonals in [16, 512], det <= 2^20 and even), forward
@@ -344,14 +385,19 @@ def run_native(args):
     ms_max, points = aggregate(ms, points_local, world)
     value = points / (ms_max * 1e-3)
 
-    wavelet = None if args.no_wavelet else bench_wavelet(pf, torch, peaks_hbm=float(measured_peaks()[0]["hbm_gbs"]))
+    peaks_hbm = float(measured_peaks()[0]["hbm_gbs"])
+    tc = None
+    if not args.no_tc:
+        plan.forward(x, y)
+        tc = bench_tc(pf, torch, x, y, ms, peaks_hbm)
+    wavelet = None if args.no_wavelet else bench_wavelet(pf, torch, peaks_hbm=peaks_hbm)
     mix = None if args.no_mix else bench_mix(pf, torch, peaks_hbm=float(measured_peaks()[0]["hbm_gbs"]))
     if args.no_e2e:
         e2e_value, e2e_ms = None, None
         plan.close()
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "points/s", "ms_per_step": ms_max,
-                              "kernels": prof, "wavelet": wavelet, "uneven_mix": mix,
+                              "kernels": prof, "tc_split": tc, "wavelet": wavelet, "uneven_mix": mix,
                               "note": "profiling run (no e2e)"}), flush=True)
         return 0
     # end to end through the public API with host buffers (pinned), per step:
@@ -408,6 +454,7 @@ def run_native(args):
             "compulsory_frac": (BYTES_PER_POINT_PASS * points_local / (ms * 1e-3) / 1e9) / peak,
             "kernels": kernels,
             "cpu_baseline": cpu,
+            "tc_split": tc,
             "wavelet": wavelet,
             "uneven_mix": mix,
             "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": int(x.numel() * 8),
@@ -434,6 +481,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--no-wavelet", action="store_true", help="skip the wavelet cascade measurement")
     ap.add_argument("--no-mix", action="store_true", help="skip the uneven pattern-mix measurement")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core form measurement")
     ap.add_argument("--batch", type=int, default=0, help="override the workload batch (profiling runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:

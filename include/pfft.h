@@ -78,6 +78,17 @@ typedef enum {
 
 enum { PFFT_C64 = 0, PFFT_C128 = 1 };
 
+/* Flags of pfft_plan_create. */
+enum {
+  /* Split-precision tensor-core form (PFFT_C64 only): the radix-16 and
+   * radix-32 stages run as dense DFT-matrix products on the tensor cores in
+   * fp16 with fp32 accumulation, each operand split into hi + lo fp16 halves
+   * (three products per tile), which recovers fp32-level accuracy.  Values
+   * entering those stages must stay below the fp16 range (|x| < 65504).
+   * Without the flag every stage runs in plain fp32 on the CUDA cores. */
+  PFFT_FLAG_TC_SPLIT = 1u
+};
+
 /* Which index map pfft_index_map returns. */
 enum {
   PFFT_MAP_INPUT_BOX = 0,   /* per input slot: y (d coordinates) in the box of H(M)     */
@@ -108,7 +119,8 @@ pfft_status pfft_smith_normal_form(int d, const int64_t* M, int64_t* Q, int64_t*
  * ------------------------------------------------------------------------- */
 
 /* Plan the transform on P(M) for `batch` signals of |det M| points each.
- * M: d*d row-major host array.  dtype: PFFT_C64 or PFFT_C128.  flags: 0.
+ * M: d*d row-major host array.  dtype: PFFT_C64 or PFFT_C128.  flags: 0 or
+ * PFFT_FLAG_TC_SPLIT (PFFT_C64 only, else PFFT_ERR_UNSUPPORTED).
  * Computes H(M), H(M^T), the Smith form and the basis of Theorem 1
  * (Section 3, eqs. (basisPM), (basisGM); Remark 2 allows any biorthogonal
  * pair, and the planner picks the one whose longest cycle runs along the

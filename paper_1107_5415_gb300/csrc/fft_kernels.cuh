@@ -18,6 +18,10 @@ namespace pfft {
 template <bool PAD>
 __device__ __forceinline__ int phys(int x) { return PAD ? x + (x >> 4) : x; }
 
+}  // namespace pfft
+#include "fft_tc.cuh"
+namespace pfft {
+
 // Multiply v[r] by w^r, w = tw[base], r = 1..R-1.  The powers w^(2^b) come
 // from the table and w^r is their product over the set bits of r, so every
 // factor carries at most log2(R) - 1 rounded multiplications.
@@ -137,7 +141,6 @@ __device__ __noinline__ void run_direct_stage(C* sm, const PassArgs& a, const St
     ebase = COLS ? base * a.T + t : t * a.L + base;
   };
   // pre-pass: twiddles and the symmetric / antisymmetric combinations
-  const int NsR = s.Ns * R;
   for (int w = threadIdx.x; w < nbfly * h; w += nthr) {
     const int r = w / nbfly + 1;
     const int b = w - (r - 1) * nbfly;
@@ -147,7 +150,7 @@ __device__ __noinline__ void run_direct_stage(C* sm, const PassArgs& a, const St
     C* p1 = sm + phys<PAD>(ebase + j * step + (R - r) * istep);
     C u = *p0, v = *p1;
     if (s.Ns > 1) {
-      const int i0 = int((int64_t(r) * k) % NsR), i1 = int((int64_t(R - r) * k) % NsR);
+      const int i0 = r * k, i1 = (R - r) * k;  // < Ns R: no reduction
       u = cmul(u, __ldg(tw + i0 * s.twstep));
       v = cmul(v, __ldg(tw + i1 * s.twstep));
     }
@@ -226,6 +229,17 @@ __device__ __noinline__ void run_direct_stage(C* sm, const PassArgs& a, const St
 template <typename C, int EPT, bool COLS, bool POW2, bool PAD>
 __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ tw) {
   int i = 0;
+  constexpr bool kC64 = sizeof(C) == 8;
+  uint32_t* tab32 = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(sm) + a.tc_off);
+  uint32_t* tab16 = tab32 + (a.cnt[kTC32Region] ? tc_words<32>() : 0);
+  if constexpr (kC64) {
+    if (a.tc) {
+      const float2* twf = reinterpret_cast<const float2*>(tw);
+      if (a.cnt[kTC32Region]) tc_build_tables<32>(tab32, twf, a.tw_n);
+      if (a.cnt[0]) tc_build_tables<16>(tab16, twf, a.tw_n);
+      __syncthreads();
+    }
+  }
   if constexpr (!POW2) {
     _Pragma("unroll 1") for (int q = 0; q < a.cnt[kDirectRegion]; ++q, ++i)
         run_direct_stage<C, kDirectItems<EPT>, COLS, PAD>(sm, a, a.st[i], tw);
@@ -233,7 +247,21 @@ __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ t
 #define PFFT_REGION(RR, IDX)                                                     \
   _Pragma("unroll 1") for (int q = 0; q < a.cnt[IDX]; ++q, ++i)                  \
       run_stage<C, RR, (EPT / RR > 0 ? EPT / RR : 1), COLS, PAD>(sm, a, a.st[i], tw);
-  PFFT_REGION(16, 0)
+  bool tc16 = false;
+  if constexpr (kC64) {
+    if (a.tc) {
+      float2* smf = reinterpret_cast<float2*>(sm);
+      const float2* twf = reinterpret_cast<const float2*>(tw);
+      _Pragma("unroll 1") for (int q = 0; q < a.cnt[kTC32Region]; ++q, ++i)
+          run_tc_stage<32, COLS, PAD>(smf, a, a.st[i], twf, tab32);
+      _Pragma("unroll 1") for (int q = 0; q < a.cnt[0]; ++q, ++i)
+          run_tc_stage<16, COLS, PAD>(smf, a, a.st[i], twf, tab16);
+      tc16 = true;
+    }
+  }
+  if (!tc16) {
+    PFFT_REGION(16, 0)
+  }
   PFFT_REGION(8, 1)
   PFFT_REGION(4, 2)
   PFFT_REGION(2, 3)

@@ -24,7 +24,7 @@ namespace {
 // kMaxDirectRadix), then 16s, the rest of the power of two and 3, 5, 7 -- the
 // execution order of the stage regions.  Returns false if a prime factor is
 // not supported.
-bool factor_radices(int n, std::vector<int>& out) {
+bool factor_radices(int n, std::vector<int>& out, bool tc = false) {
   out.clear();
   for (int p = kMinDirectRadix; p <= kMaxDirectRadix && p <= n; p += 2) {
     bool prime = true;
@@ -43,6 +43,10 @@ bool factor_radices(int n, std::vector<int>& out) {
   while (n % 2 == 0) {
     n /= 2;
     ++p2;
+  }
+  while (tc && p2 >= 5) {  // tensor-core passes: radix-32 stages first
+    out.push_back(32);
+    p2 -= 5;
   }
   while (p2 >= 4) {
     out.push_back(16);
@@ -75,9 +79,9 @@ void set_box(BoxDesc& B, const IMat& H) {
 // Stages of a Stockham DFT along one pencil axis of length a and stride
 // sigma, in the radix order of kRadixOrder (Ns accumulates in that order);
 // twiddles come from a table of order nD (a multiple of a).
-bool axis_stages(std::vector<StageDesc>& out, int a, int sigma, int nD) {
+bool axis_stages(std::vector<StageDesc>& out, int a, int sigma, int nD, bool tc) {
   std::vector<int> rad;
-  if (!factor_radices(a, rad)) return false;
+  if (!factor_radices(a, rad, tc)) return false;
   int Ns = 1;
   for (int R : rad) {
     StageDesc s;
@@ -100,13 +104,14 @@ bool axis_stages(std::vector<StageDesc>& out, int a, int sigma, int nD) {
 int radix_region(int R) {
   for (int i = 0; i < kDirectRegion; ++i)
     if (kRadixOrder[i] == R) return i;
+  if (R == 32) return kTC32Region;
   return R >= kMinDirectRadix && R <= kMaxDirectRadix ? kDirectRegion : -1;
 }
 
-// Execution order of the regions: direct prime stages first.
+// Execution order of the regions: direct prime stages first, then radix 32.
 int region_rank(int R) {
   const int reg = radix_region(R);
-  return reg == kDirectRegion ? -1 : reg;
+  return reg == kDirectRegion ? -2 : reg == kTC32Region ? -1 : reg;
 }
 
 // Merge the stages of all axes, grouped by radix region (stable, so each
@@ -178,13 +183,13 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
   std::vector<StageDesc> stg;
   if (!cols) {
     p.L = P.nD;
-    if (!axis_stages(stg, P.nD, 1, P.nD)) return PFFT_ERR_UNSUPPORTED;
+    if (!axis_stages(stg, P.nD, 1, P.nD, P.tc)) return PFFT_ERR_UNSUPPORTED;
     p.groups = (P.LB + T - 1) / T;
   } else {
     p.L = P.LB;
     int sigma = 1;
     for (int s = int(P.pen.size()) - 1; s >= 0; --s) {  // pencil axes, last fastest
-      if (!axis_stages(stg, P.pen[s], sigma, p.tw_n)) return PFFT_ERR_UNSUPPORTED;
+      if (!axis_stages(stg, P.pen[s], sigma, p.tw_n, P.tc)) return PFFT_ERR_UNSUPPORTED;
       sigma *= P.pen[s];
     }
     p.groups = (P.nD + T - 1) / T;
@@ -232,6 +237,12 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
   p.pad = rmax ? 0 : 1;
   p.dir_off = p.pad ? (nel - 1) + ((nel - 1) >> 4) + 1 : nel;
   p.smem_bytes = int(size_t(p.dir_off + rmax) * elem_bytes(P.dtype));
+  p.tc = P.tc ? 1 : 0;
+  p.tc_off = (p.smem_bytes + 15) & ~15;
+  if (p.tc) {  // fragment tables of the radix-32 / 16 tensor-core stages (fft_tc.cuh)
+    const int w32 = 2 * 16 * 32 * 4, w16 = 2 * 4 * 32 * 4;
+    p.smem_bytes = p.tc_off + 4 * ((p.cnt[kTC32Region] ? w32 : 0) + (p.cnt[0] ? w16 : 0));
+  }
   if (p.smem_bytes > 227 * 1024) return PFFT_ERR_UNSUPPORTED;
   return PFFT_OK;
 }
@@ -703,13 +714,18 @@ static void release(pfft_plan_s* P) { plan_release(P); }
 extern "C" pfft_status pfft_plan_create(pfft_plan* out, int d, const int64_t* M, int64_t batch,
                                         int dtype, unsigned flags) {
   if (!out || !M || batch < 1 || batch > 65535 || (dtype != PFFT_C64 && dtype != PFFT_C128) ||
-      flags != 0)
+      (flags & ~unsigned(PFFT_FLAG_TC_SPLIT)))
     return PFFT_ERR_ARG;
+  if ((flags & PFFT_FLAG_TC_SPLIT) && dtype != PFFT_C64) return PFFT_ERR_UNSUPPORTED;
   *out = nullptr;
   pfft_plan_s* P = new (std::nothrow) pfft_plan_s;
   if (!P) return PFFT_ERR_OOM;
   P->batch = batch;
   P->dtype = dtype;
+  if (flags & PFFT_FLAG_TC_SPLIT) {
+    P->tc = true;
+    P->generic_only = true;
+  }
   pfft_status st;
   try {
     st = plan_host(*P, d, M);

@@ -36,6 +36,9 @@ constexpr int kRadixOrder[7] = {16, 8, 4, 2, 3, 5, 7};
 // memory (run_direct_stage; a register butterfly of that size spills); they
 // run before all others, so the first one of each axis needs no twiddles.
 constexpr int kDirectRegion = 7;
+// Radix-32 stages exist only in split-precision tensor-core passes (fft_tc.cuh);
+// there the radix-16 stages run on the tensor cores too.
+constexpr int kTC32Region = 8;
 constexpr int kMinDirectRadix = 11;
 constexpr int kMaxDirectRadix = 1021;
 // Output pairs a thread holds in a direct stage: a butterfly of radix R >= 11
@@ -63,7 +66,9 @@ struct alignas(16) PassArgs {
   int ts;       // int32 per table entry: 2 (d <= 2) or 4 (d = 3, 4)
   int cols;     // 1: column pass, 0: row pass
   int nstages;
-  int cnt[8];  // stages per radix, in the order of kRadixOrder; [7]: direct prime stages
+  int cnt[9];  // stages per radix, in the order of kRadixOrder; [7]: direct prime stages; [8]: radix 32
+  int tc;       // 1: radix-16 / 32 stages on the tensor cores in split fp16 (complex64)
+  int tc_off;   // byte offset of the tensor-core fragment tables in shared memory
   int dir_off;  // shared-memory element offset of the omega_R table of a direct stage
   int pad;      // 1: padded shared-memory tile (x + x / 16); 0 when the pass has direct stages
   int pow2;     // all radices are powers of two

@@ -31,6 +31,7 @@ struct pfft_plan_s {
   pfft::Arena* arena = nullptr;  // sub-allocate device tables here (batch plans)
   bool generic_only = false;     // shared-memory Stockham kernels only (grouped launches)
   bool own_workspace = true;     // allocate the LB x nD workspace
+  bool tc = false;               // split-precision tensor-core radix-16 / 32 stages
   // device state
   int device = 0;
   int* dtab = nullptr;
