@@ -670,6 +670,17 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
       if (int e_ = P.alloc((void**)&P.runs, flat.size() * sizeof(int))) return pfft_status(e_);
       cudaMemcpy(P.runs, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice);
       P.rowp.tma = 1;
+      // padded workspace-order staging (fft_tma.cuh): 2^lg blocks of one
+      // span each, offset so that blocks start 32 / 2^lg banks apart (16-byte
+      // multiples for the bulk copies)
+      P.rowp.stg_pad = 0;
+      if (P.rowp.pi_arith && P.rowp.pi_lg > 0 && P.rowp.pi_lg <= 6 && P.rowp.pi_lspan >= 2) {
+        const int esz = int(elem_bytes(P.dtype));
+        const int pad = std::max(16, 128 >> P.rowp.pi_lg) / esz;  // elements
+        const int nel = P.rowp.T * P.rowp.L;
+        const int stage_end = nel + (1 << P.rowp.pi_lg) * pad;
+        if (stage_end <= P.rowp.stw_smem_off) P.rowp.stg_pad = pad;  // fits before the stage table
+      }
       P.rowp.runs = P.runs;
       P.rowp.nruns = maxr;
       P.rowp.bar_smem_off = (P.rowp.smem_bytes + 15) & ~15;

@@ -99,6 +99,10 @@ struct alignas(16) PassArgs {
   int nruns;
   int bar_smem_off;   // byte offset of the mbarrier in shared memory
   int* status;        // device status word (PFFT_ERR_TIMEOUT on a timed-out wait)
+  // workspace-order staging of the TMA row pass in 2^pi_lg blocks of 2^pi_lspan
+  // positions, each followed by stg_pad elements (0: one dense block), so that
+  // the permuted accesses of lanes with equal mu >> pi_lg hit different banks
+  int stg_pad;
   StageDesc st[kMaxStages];
   FastDiv divT, divnD;
   int nthreads;

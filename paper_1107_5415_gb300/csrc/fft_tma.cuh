@@ -90,13 +90,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_tma_kernel(PassArgs a) {
   // ---- stage the row in shared memory (dense, element or position order)
   if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, uint32_t(L) * uint32_t(sizeof(C)));
   __syncthreads();
+  // workspace-order staging: block c of 2^pi_lg holds positions [c span, (c+1) span)
+  const int nblk = a.stg_pad ? (1 << a.pi_lg) : 1;
+  const int span = L / nblk;
+  auto spos = [&](int pos) { return a.stg_pad ? pos + (pos >> a.pi_lspan) * a.stg_pad : pos; };
   if (a.load_mode == MAP_BOX_H) {
     if (threadIdx.x < a.nruns) {
       const int4 r = __ldg(runs + threadIdx.x);
       if (r.z > 0) bulk_g2s(sm + r.x, in + r.y, uint32_t(r.z) * uint32_t(sizeof(C)), bar);
     }
-  } else if (threadIdx.x == 0) {
-    bulk_g2s(sm, in + (size_t)row * a.nD, uint32_t(L) * uint32_t(sizeof(C)), bar);
+  } else if (threadIdx.x < nblk) {
+    const int c = threadIdx.x;
+    bulk_g2s(sm + c * (span + a.stg_pad), in + (size_t)row * a.nD + c * span, uint32_t(span) * uint32_t(sizeof(C)),
+             bar);
   }
   if (!mbar_wait_bounded(bar, 0)) {
     if (threadIdx.x == 0) atomicExch(a.status, kStatusTimeout);
@@ -110,7 +116,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_tma_kernel(PassArgs a) {
     for (int k = 0; k < R; ++k) v[k] = sm[p + P * k];
   } else {
 #pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = sm[col_pos(a, p + P * k)];
+    for (int k = 0; k < R; ++k) v[k] = sm[spos(col_pos(a, p + P * k))];
   }
   if (a.conj_in) {
 #pragma unroll
@@ -131,7 +137,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_tma_kernel(PassArgs a) {
       for (int k = 0; k < R; ++k) v[k] = cmul(v[k], fs_twiddle<C>(a, row, p + P * k));
     }
 #pragma unroll
-    for (int k = 0; k < R; ++k) sm[col_pos(a, p + P * k)] = v[k];
+    for (int k = 0; k < R; ++k) sm[spos(col_pos(a, p + P * k))] = v[k];
   } else {
     const Rl sc = Rl(a.scale);
 #pragma unroll
@@ -140,8 +146,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_tma_kernel(PassArgs a) {
   fence_async_smem();
   __syncthreads();
   if (a.store_mode == MAP_WS) {
-    if (threadIdx.x == 0) {
-      bulk_s2g(out + (size_t)row * a.nD, sm, uint32_t(L) * uint32_t(sizeof(C)));
+    if (threadIdx.x < nblk) {
+      const int c = threadIdx.x;
+      bulk_s2g(out + (size_t)row * a.nD + c * span, sm + c * (span + a.stg_pad), uint32_t(span) * uint32_t(sizeof(C)));
       bulk_commit();
       bulk_wait_read_all();
     }
