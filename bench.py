@@ -276,6 +276,86 @@ def bench_tc(pf, torch, x, y_fp32, ms_fp32, peaks_hbm, steps=50, warmup=5):
             "compulsory_frac": BYTES_PER_POINT_PASS * pts / (ms * 1e-3) / 1e9 / peaks_hbm}
 
 
+TABLE1_I = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 0]
+
+
+def _time_ms(torch, fn, steps, warmup):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def bench_table1(pf, torch, peaks_hbm, steps=20, warmup=3):
+    """The pattern family of Table 1 (Section 6.1): M = [[2048, i], [0, 2048]]
+    for every divisor i of 2048 (i = 0 last), 2^22 points, forward transforms
+    of 8 signals per launch (256 MiB, larger than L2).  The factor is the
+    time against the 1-D transform of 2^22 points by this library
+    (M = [[2^22]]), the comparison the table's factor column makes; the
+    library 1-D FFT of torch (cuFFT) is listed as context."""
+    w = SI.WORKLOADS["table1"]
+    n, batch = w["n"], w["batch"]
+    m = n * n
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w["seed"])
+    x = torch.randn(batch, m, dtype=torch.complex64, device="cuda", generator=gen) * math.sqrt(2.0)
+    y = torch.empty_like(x)
+
+    def run(M):
+        plan = pf.PatternFFT(M, batch)
+        ms = _time_ms(torch, lambda: plan.forward(x, y), steps, warmup)
+        plan.close()
+        return ms
+
+    ms_1d = run([[m]])
+    ms_cufft = _time_ms(torch, lambda: torch.fft.fft(x, dim=1, norm="ortho"), steps, warmup)
+    rows = []
+    for i in TABLE1_I:
+        ms = run([[n, i], [0, n]])
+        rows.append({"i": i, "ms_per_transform": ms / batch, "factor_vs_1d": ms / ms_1d,
+                     "achieved_gbs_2pass": 2 * 16 * batch * m / (ms * 1e-3) / 1e9})
+    return {"workload": "Table 1 family M = [[2048, i], [0, 2048]], 2^22 points, 8 signals per launch",
+            "one_d_ms_per_transform": ms_1d / batch, "cufft_1d_ms_per_transform": ms_cufft / batch,
+            "rows": rows}
+
+
+def bench_directional(pf, torch, peaks_hbm, steps=20, warmup=3):
+    """One split level of M = 512 I by each dilation of Section 6.2's set
+    {J_x, J_y, J_d} (Dirichlet symbol), 16 signals of anisotropic synthetic
+    coefficients c_h = (1 + h_1^2 + 16 h_2^2)^{-1} z_h (h centred, z complex
+    N(0,1) seeded); per dilation the time and the share of the energy that
+    lands in the wavelet part."""
+    w = SI.WORKLOADS["directional"]
+    M, batch = w["M"], w["batch"]
+    n = M[0][0]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w["seed"])
+    h = torch.arange(n, device="cuda", dtype=torch.float32)
+    h = torch.where(h >= n // 2, h - n, h)
+    wt = 1.0 / (1.0 + h[:, None] ** 2 + 16.0 * h[None, :] ** 2)
+    c = (torch.randn(batch, n * n, dtype=torch.complex64, device="cuda", generator=gen) * math.sqrt(2.0)
+         * wt.reshape(1, -1))
+    e_c = torch.linalg.vector_norm(c).item() ** 2
+    out = {"workload": "one split level, M = 512 I, J in {J_x, J_y, J_d}, batch 16, anisotropic coefficients"}
+    for name, J in SI.DIRECTIONAL_J.items():
+        plan = pf.WaveletSplit(M, [J], pf.PWT_DIRICHLET, 0.125, batch)
+        sc, wv = plan.decompose(c)
+        ms = _time_ms(torch, lambda: plan.decompose(c), steps, warmup)
+        e_w = torch.linalg.vector_norm(wv[0]).item() ** 2
+        out[name] = {"J": J, "ms": ms, "wavelet_energy_share": e_w / e_c,
+                     "achieved_gbs": 16 * batch * n * n / (ms * 1e-3) / 1e9}
+        plan.close()
+    return out
+
+
 def bench_mix(pf, torch, peaks_hbm, steps=10, warmup=3):
     """Uneven serving-style mix: 4096 seeded patterns (d in {2, 3}, upper
     triangular, diagonals in [16, 512], det <= 2^20 and even), forward
@@ -391,13 +471,16 @@ def run_native(args):
         plan.forward(x, y)
         tc = bench_tc(pf, torch, x, y, ms, peaks_hbm)
     wavelet = None if args.no_wavelet else bench_wavelet(pf, torch, peaks_hbm=peaks_hbm)
-    mix = None if args.no_mix else bench_mix(pf, torch, peaks_hbm=float(measured_peaks()[0]["hbm_gbs"]))
+    mix = None if args.no_mix else bench_mix(pf, torch, peaks_hbm=peaks_hbm)
+    table1 = None if args.no_table1 else bench_table1(pf, torch, peaks_hbm)
+    directional = None if args.no_directional else bench_directional(pf, torch, peaks_hbm)
     if args.no_e2e:
         e2e_value, e2e_ms = None, None
         plan.close()
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "points/s", "ms_per_step": ms_max,
                               "kernels": prof, "tc_split": tc, "wavelet": wavelet, "uneven_mix": mix,
+                              "table1": table1, "directional": directional,
                               "note": "profiling run (no e2e)"}), flush=True)
         return 0
     # end to end through the public API with host buffers (pinned), per step:
@@ -457,6 +540,8 @@ def run_native(args):
             "tc_split": tc,
             "wavelet": wavelet,
             "uneven_mix": mix,
+            "table1": table1,
+            "directional": directional,
             "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": int(x.numel() * 8),
                     "d2h_bytes_per_step": int(z.numel() * 8)},
             "gpu_launches": 4 * args.steps,
@@ -482,6 +567,8 @@ def main(argv=None):
     ap.add_argument("--no-wavelet", action="store_true", help="skip the wavelet cascade measurement")
     ap.add_argument("--no-mix", action="store_true", help="skip the uneven pattern-mix measurement")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core form measurement")
+    ap.add_argument("--no-table1", action="store_true", help="skip the Table 1 pattern sweep")
+    ap.add_argument("--no-directional", action="store_true", help="skip the directional dilation comparison")
     ap.add_argument("--batch", type=int, default=0, help="override the workload batch (profiling runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -20,6 +20,9 @@ M_AUTOGRAD_TINY = [[4, 1, 0], [0, 4, 1], [0, 0, 4]]         # det 64, one cycle 
 M_WAVELET_2D = [[1024, 1024], [-1024, 1024]]                # 2^10 [[1,1],[-1,1]], det 2^21
 J_DIAG_A = [[1, 1], [-1, 1]]
 J_DIAG_B = [[1, -1], [1, 1]]
+# the dilation set of Section 6.2 (J_x, J_y, J_d) and the pattern it is applied to
+DIRECTIONAL_J = {"J_x": [[2, 0], [0, 1]], "J_y": [[1, 0], [0, 2]], "J_d": [[1, -1], [1, 1]]}
+M_DIRECTIONAL = [[512, 0], [0, 512]]
 
 WORKLOADS = {
     "small_2d": dict(M=M_SMALL_2D, batch=1, seed=0),
@@ -27,6 +30,8 @@ WORKLOADS = {
     "autograd_3d": dict(M=M_AUTOGRAD_3D, batch=4, seed=2),
     "wavelet_2d": dict(M=M_WAVELET_2D, batch=16, seed=3, levels=12),
     "uneven_mix": dict(n_patterns=4096, seed=4, even_det=True),
+    "directional": dict(M=M_DIRECTIONAL, batch=16, seed=5),
+    "table1": dict(n=2048, batch=8, seed=6),
 }
 
 SAMPLE_SEED = 12345

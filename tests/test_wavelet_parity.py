@@ -20,7 +20,11 @@ CASES = [([[8, 8], [-8, 8]], [SI.J_DIAG_A]), ([[8, 0], [0, 8]], [[[2, 0], [0, 1]
          ([[16, 16], [-16, 16]], SI.wavelet_dilations(5)),
          ([[12, 4], [0, 10]], [[[2, 0], [0, 1]], [[1, 0], [0, 2]]]),
          ([[4, 1, 0], [0, 4, 1], [0, 0, 4]], [[[1, 0, 0], [0, 1, 0], [0, 0, 2]]]),
-         ([[8, 2, 0], [0, 4, 2], [0, 0, 6]], [[[2, 0, 0], [0, 1, 0], [0, 0, 1]], [[1, 0, 0], [0, 2, 0], [0, 0, 1]]])]
+         ([[8, 2, 0], [0, 4, 2], [0, 0, 6]], [[[2, 0, 0], [0, 1, 0], [0, 0, 1]], [[1, 0, 0], [0, 2, 0], [0, 0, 1]]]),
+         # dilations whose symbol cube does not contain [-1/2, 1/2]^d (parity dilations)
+         ([[3, 1], [1, 3]], [[[1, 0], [-1, 2]]]),
+         ([[10, 1, 7], [0, 9, 1], [0, 0, 32]], [[[1, 0, 0], [-1, 2, 0], [0, 0, 1]]]),
+         ([[6, 1, 1], [0, 5, 1], [0, 0, 4]], [[[1, 0, 0], [0, 1, 0], [-1, -1, 2]]])]
 
 
 def _gpu(x, dt=torch.complex64):
@@ -112,3 +116,22 @@ def test_wavelet_argument_errors():
     with pytest.raises(pf.PfftError) as e:
         pf.WaveletSplit([[8, 0], [0, 8]], [[[3, 0], [0, 1]]])
     assert e.value.status == 5
+
+
+@pytest.mark.parametrize("name", list(SI.DIRECTIONAL_J))
+@pytest.mark.parametrize("sym", ["dirichlet", "dlvp"])
+def test_directional_dilations_one_level(name, sym):
+    """One split level of M = 512 I by each dilation of the set of Section 6.2
+    (J_x, J_y, J_d), on seeded coefficients, every output against the oracle;
+    perfect reconstruction on the GPU."""
+    w = SI.WORKLOADS["directional"]
+    M, J = w["M"], SI.DIRECTIONAL_J[name]
+    gsym, osym = SYM[sym]
+    plan = pf.WaveletSplit(M, [J], gsym, 0.125, 2)
+    c = SI.complex_normal(2, plan.sizes[0], w["seed"])
+    s_gpu, w_gpu = plan.decompose(_gpu(c))
+    d1, d2 = oracle.wavelet_level(M, J, osym, 0.125, c_hat=c)
+    assert rel_l2(s_gpu.cpu().numpy(), d1) <= 1e-5
+    assert rel_l2(w_gpu[0].cpu().numpy(), d2) <= 1e-5
+    back = plan.reconstruct(s_gpu, w_gpu).cpu().numpy()
+    assert rel_l2(back, c) <= 1e-5
