@@ -48,14 +48,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1) grouped_pass_kernel(GroupArgs 
   C* sm = reinterpret_cast<C*>(smem_raw);
   if constexpr (COLS) {
     if (a.pad)
-      col_pass_body<C, EPT, false, true>(a, tile, 0, sm);
+      col_pass_body<C, EPT, false, true, false>(a, tile, 0, sm);
     else
-      col_pass_body<C, EPT, false, false>(a, tile, 0, sm);
+      col_pass_body<C, EPT, false, false, false>(a, tile, 0, sm);
   } else {
     if (a.pad)
-      row_pass_body<C, EPT, false, true>(a, tile, 0, sm);
+      row_pass_body<C, EPT, false, true, false>(a, tile, 0, sm);
     else
-      row_pass_body<C, EPT, false, false>(a, tile, 0, sm);
+      row_pass_body<C, EPT, false, false, false>(a, tile, 0, sm);
   }
 }
 

@@ -96,128 +96,216 @@ __device__ __forceinline__ void run_stage(C* sm, const PassArgs& a, const StageD
   __syncthreads();
 }
 
-// One stage of a prime radix R >= 11, evaluated directly.  With
-// x'_r = x_r exp(-2 pi i r k / (Ns R)) (k = j mod Ns; no twiddle when Ns = 1)
-// and h = (R - 1) / 2, a pre-pass forms, in place,
-//     a_r = x'_r + x'_{R-r}  (slot r),   b_r = x'_r - x'_{R-r}  (slot R - r),   r = 1..h,
-// and since omega_R^{(R-r) s} = conj(omega_R^{r s}), outputs s and R - s are
-//     y_s     = x_0 + sum_{r=1..h} (a_r c_rs - i b_r s_rs),
-//     y_{R-s} = x_0 + sum_{r=1..h} (a_r c_rs + i b_r s_rs),
-// c_rs - i s_rs = omega_R^{r s}: one work item accumulates the four real sums
-// of the pair in h steps.  Lanes of a warp take consecutive butterflies of
-// the same output pair, so the a, b reads are consecutive and the omega_R
-// reads (a table of R entries after the tile) are broadcasts.  Every read of
-// the stage happens before its first write.
-template <typename C, int NBI, bool COLS, bool PAD>
-__device__ __noinline__ void run_direct_stage(C* sm, const PassArgs& a, const StageDesc& s,
-                                              const C* __restrict__ tw) {
+// One stage of a prime radix R >= 11, evaluated directly, in the order of a
+// primitive root g of R.  With x'_r = x_r exp(-2 pi i r k / (Ns R))
+// (k = j mod Ns; none when Ns = 1), h = (R - 1) / 2 and r_m = g^m mod R, so
+// that R - r_m = r_{m+h}, a pre-pass forms
+//     a_m = x'_{r_m} + x'_{R - r_m},   b_m = x'_{r_m} - x'_{R - r_m},   m < h,
+// and stores them at slots 1 + m and 1 + h + m of the butterfly (slot 0 keeps
+// x_0).  For an output q = r_n (n < h), r_m q = g^{m+n}, so with the table
+// P[t] = omega_R^{g^t} = c_t - i s_t (t < R - 1)
+//     y_q     = x_0 + sum_m (a_m c_{m+n} - i b_m s_{m+n}),
+//     y_{R-q} = x_0 + sum_m (a_m c_{m+n} + i b_m s_{m+n}),
+// because omega_R^{(R - r) q} is the conjugate of omega_R^{r q}; y_0 is x_0 plus
+// the sum of the a_m.  A work item takes Q consecutive outputs n of one
+// butterfly: per step m it reads a_m and b_m once (consecutive addresses
+// across the lanes, which take consecutive butterflies) and Q table entries
+// P[m + n] (broadcasts) for 4Q FMAs, with no index arithmetic.  Every read of
+// a phase happens before the barrier that precedes its writes.
+template <bool COLS>
+__device__ __forceinline__ void direct_locate(const PassArgs& a, const StageDesc& s, int b, int& ebase, int& k,
+                                              int& j) {
+  const int per_pencil = a.L / s.R;
+  int t, rest;
+  if (COLS) {
+    rest = a.divT.div(b);
+    t = b - rest * a.T;
+  } else {
+    t = b / per_pencil;
+    rest = b - t * per_pencil;
+  }
+  const int o = s.div_aR.div(rest);
+  j = rest - o * s.aR;
+  const int hi = s.div_sigma.div(o);
+  const int base = hi * s.a * s.sigma + (o - hi * s.sigma);
+  k = j - s.div_Ns.div(j) * s.Ns;
+  ebase = COLS ? base * a.T + t : t * a.L + base;
+}
+
+// y_0 and the output pairs of a direct stage whose a_m, b_m are in place.
+template <typename C, int NQ, int Q, bool COLS, bool PAD>
+__device__ __noinline__ void direct_pairs(C* sm, const PassArgs& a, const StageDesc& s, const C* P, const int* gp) {
   using Rl = decltype(C::x);
   const int R = s.R;
   const int h = (R - 1) / 2;
-  const int per_pencil = a.L / R;
-  const int nbfly = a.T * per_pencil;
-  const int npair = (R + 1) / 2;
+  const int nbfly = a.T * (a.L / R);
+  const int step = s.sigma * (COLS ? a.T : 1);
+  const int istep = s.aR * step;
   const int nthr = blockDim.x;
-  const int escale = COLS ? a.T : 1;
-  const int step = s.sigma * escale;
-  const int istep = s.aR * step;  // element distance of consecutive inputs r
-  C* W = sm + a.dir_off;
-  const int wstride = a.tw_n / R;
-  for (int e = threadIdx.x; e < R; e += nthr) W[e] = __ldg(tw + e * wstride);
-  auto locate = [&](int b, int& ebase, int& k, int& j) {
-    int t, rest;
-    if (COLS) {
-      rest = a.divT.div(b);
-      t = b - rest * a.T;
-    } else {
-      t = b / per_pencil;
-      rest = b - t * per_pencil;
-    }
-    const int o = s.div_aR.div(rest);
-    j = rest - o * s.aR;
-    const int hi = s.div_sigma.div(o);
-    const int base = hi * s.a * s.sigma + (o - hi * s.sigma);
-    k = j - s.div_Ns.div(j) * s.Ns;
-    ebase = COLS ? base * a.T + t : t * a.L + base;
-  };
-  // pre-pass: twiddles and the symmetric / antisymmetric combinations
-  for (int w = threadIdx.x; w < nbfly * h; w += nthr) {
-    const int r = w / nbfly + 1;
-    const int b = w - (r - 1) * nbfly;
-    int ebase, k, j;
-    locate(b, ebase, k, j);
-    C* p0 = sm + phys<PAD>(ebase + j * step + r * istep);
-    C* p1 = sm + phys<PAD>(ebase + j * step + (R - r) * istep);
-    C u = *p0, v = *p1;
-    if (s.Ns > 1) {
-      const int i0 = r * k, i1 = (R - r) * k;  // < Ns R: no reduction
-      u = cmul(u, __ldg(tw + i0 * s.twstep));
-      v = cmul(v, __ldg(tw + i1 * s.twstep));
-    }
-    *p0 = cadd(u, v);
-    *p1 = csub(u, v);
-  }
-  __syncthreads();
-  C y0[NBI], y1[NBI];
-  int ob[NBI], qs[NBI];
+  const int nblk = (h + Q - 1) / Q;
+  auto locate = [&](int b, int& ebase, int& k, int& j) { direct_locate<COLS>(a, s, b, ebase, k, j); };
+  C y0s[kDirectZero];
+  int z0[kDirectZero];
 #pragma unroll
-  for (int u = 0; u < NBI; ++u) {
+  for (int u = 0; u < kDirectZero; ++u) {
+    const int b = threadIdx.x + u * nthr;
+    z0[u] = -1;
+    if (b < nbfly) {
+      int ebase, k, j;
+      locate(b, ebase, k, j);
+      const int i0 = ebase + j * step;
+      C acc0 = sm[phys<PAD>(i0)];
+      for (int m = 0; m < h; ++m) acc0 = cadd(acc0, sm[phys<PAD>(i0 + (1 + m) * istep)]);
+      y0s[u] = acc0;
+      z0[u] = ebase + ((j - k) * R + k) * step;
+    }
+  }
+  Rl acc[NQ][Q][4];
+  int ob[NQ], n0[NQ];
+#pragma unroll
+  for (int u = 0; u < NQ; ++u) {
     const int w = threadIdx.x + u * nthr;
     ob[u] = -1;
-    if (w < nbfly * npair) {
-      const int q = w / nbfly;
-      const int b = w - q * nbfly;
+    n0[u] = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) acc[u][i][0] = acc[u][i][1] = acc[u][i][2] = acc[u][i][3] = Rl(0);
+    if (w < nbfly * nblk) {
+      const int blk = w / nbfly;
+      const int b = w - blk * nbfly;
       int ebase, k, j;
       locate(b, ebase, k, j);
       const int i0 = ebase + j * step;
       const C x0 = sm[phys<PAD>(i0)];
-      Rl P1 = x0.x, P3 = x0.y, P2 = 0, P4 = 0;
-      int idx = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        acc[u][i][0] = x0.x;
+        acc[u][i][2] = x0.y;
+      }
+      const C* pt = P + blk * Q;
       if constexpr (PAD) {
-#pragma unroll 4
-        for (int r = 1; r <= h; ++r) {
-          idx += q;
-          if (idx >= R) idx -= R;
-          const C av = sm[phys<PAD>(i0 + r * istep)];
-          const C bv = sm[phys<PAD>(i0 + (R - r) * istep)];
-          const C wv = W[idx];  // (c, -s)
-          P1 = fma(av.x, wv.x, P1);
-          P2 = fma(bv.y, wv.y, P2);  // -sum b.im s
-          P3 = fma(av.y, wv.x, P3);
-          P4 = fma(bv.x, wv.y, P4);  // -sum b.re s
+        for (int m = 0; m < h; ++m) {
+          const C av = sm[phys<PAD>(i0 + (1 + m) * istep)];
+          const C bv = sm[phys<PAD>(i0 + (1 + h + m) * istep)];
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const C wv = pt[m + i];
+            acc[u][i][0] = fma(av.x, wv.x, acc[u][i][0]);
+            acc[u][i][1] = fma(bv.y, wv.y, acc[u][i][1]);
+            acc[u][i][2] = fma(av.y, wv.x, acc[u][i][2]);
+            acc[u][i][3] = fma(bv.x, wv.y, acc[u][i][3]);
+          }
         }
       } else {
         const C* pa = sm + i0 + istep;
-        const C* pb = sm + i0 + (R - 1) * istep;
-#pragma unroll 4
-        for (int r = 1; r <= h; ++r) {
-          idx += q;
-          if (idx >= R) idx -= R;
-          const C av = *pa, bv = *pb, wv = W[idx];
+        const C* pb = sm + i0 + (1 + h) * istep;
+#pragma unroll 2
+        for (int m = 0; m < h; ++m) {
+          const C av = *pa, bv = *pb;
           pa += istep;
-          pb -= istep;
-          P1 = fma(av.x, wv.x, P1);
-          P2 = fma(bv.y, wv.y, P2);
-          P3 = fma(av.y, wv.x, P3);
-          P4 = fma(bv.x, wv.y, P4);
+          pb += istep;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const C wv = pt[m + i];  // (c, -s) of g^{m + n}
+            acc[u][i][0] = fma(av.x, wv.x, acc[u][i][0]);
+            acc[u][i][1] = fma(bv.y, wv.y, acc[u][i][1]);  // -sum b.im s
+            acc[u][i][2] = fma(av.y, wv.x, acc[u][i][2]);
+            acc[u][i][3] = fma(bv.x, wv.y, acc[u][i][3]);  // -sum b.re s
+          }
         }
       }
-      y0[u] = cmake<C>(P1 - P2, P3 + P4);  // output q
-      y1[u] = cmake<C>(P1 + P2, P3 - P4);  // output R - q
       ob[u] = ebase + ((j - k) * R + k) * step;
-      qs[u] = q;
+      n0[u] = blk * Q;
     }
   }
   __syncthreads();
   const int ostep = s.Ns * step;
 #pragma unroll
-  for (int u = 0; u < NBI; ++u) {
-    if (ob[u] >= 0) {
-      sm[phys<PAD>(ob[u] + qs[u] * ostep)] = y0[u];
-      if (qs[u] > 0) sm[phys<PAD>(ob[u] + (R - qs[u]) * ostep)] = y1[u];
+  for (int u = 0; u < kDirectZero; ++u)
+    if (z0[u] >= 0) sm[phys<PAD>(z0[u])] = y0s[u];
+#pragma unroll
+  for (int u = 0; u < NQ; ++u) {
+    if (ob[u] < 0) continue;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int n = n0[u] + i;
+      if (n >= h) break;
+      const int q = gp[n];
+      sm[phys<PAD>(ob[u] + q * ostep)] = cmake<C>(acc[u][i][0] - acc[u][i][1], acc[u][i][2] + acc[u][i][3]);
+      sm[phys<PAD>(ob[u] + (R - q) * ostep)] = cmake<C>(acc[u][i][0] + acc[u][i][1], acc[u][i][2] - acc[u][i][3]);
     }
   }
   __syncthreads();
+}
+
+template <typename C, int EPT, bool COLS, bool PAD>
+__device__ __noinline__ void run_direct_stage(C* sm, const PassArgs& a, const StageDesc& s,
+                                              const C* __restrict__ tw) {
+  constexpr int NA = kDirectPre<EPT>;
+  const int R = s.R;
+  const int h = (R - 1) / 2;
+  const int per_pencil = a.L / R;
+  const int nbfly = a.T * per_pencil;
+  const int nthr = blockDim.x;
+  const int escale = COLS ? a.T : 1;
+  const int step = s.sigma * escale;
+  const int istep = s.aR * step;  // element distance of consecutive slots
+  // tables after the tile: P[t] = omega_R^{g^t} (R - 1 complex), then g^t mod R (R - 1 int)
+  C* P = sm + a.dir_off;
+  int* gp = reinterpret_cast<int*>(P + (R - 1));
+  const int wstride = a.tw_n / R;
+  for (int e = threadIdx.x; e < R - 1; e += nthr) {
+    int pw = 1, base = s.gen, x = e;  // g^e mod R by squaring (R <= 1021: products < 2^20)
+    while (x) {
+      if (x & 1) pw = pw * base % R;
+      base = base * base % R;
+      x >>= 1;
+    }
+    gp[e] = pw;
+    P[e] = __ldg(tw + pw * wstride);
+  }
+  __syncthreads();
+  auto locate = [&](int b, int& ebase, int& k, int& j) { direct_locate<COLS>(a, s, b, ebase, k, j); };
+  // ---- pre-pass: read x_{r_m}, x_{R - r_m} (twiddled), then store a_m, b_m in m order
+  {
+    C av[NA], bv[NA];
+    int dst[NA];
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const int w = threadIdx.x + u * nthr;
+      dst[u] = -1;
+      if (w < nbfly * h) {
+        const int m = w / nbfly;
+        const int b = w - m * nbfly;
+        int ebase, k, j;
+        locate(b, ebase, k, j);
+        const int i0 = ebase + j * step;
+        const int r = gp[m];
+        C x0 = sm[phys<PAD>(i0 + r * istep)];
+        C x1 = sm[phys<PAD>(i0 + (R - r) * istep)];
+        if (s.Ns > 1) {  // r k < Ns R: no reduction
+          x0 = cmul(x0, __ldg(tw + (r * k) * s.twstep));
+          x1 = cmul(x1, __ldg(tw + ((R - r) * k) * s.twstep));
+        }
+        av[u] = cadd(x0, x1);
+        bv[u] = csub(x0, x1);
+        dst[u] = i0 + (1 + m) * istep;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      if (dst[u] >= 0) {
+        sm[phys<PAD>(dst[u])] = av[u];
+        sm[phys<PAD>(dst[u] + h * istep)] = bv[u];
+      }
+    }
+    __syncthreads();
+  }
+  // ---- y_0 = x_0 + sum_m a_m and the output pairs
+  if (R >= kDirectQ4MinRadix)
+    direct_pairs<C, kDirectQ4Items<EPT>, 4, COLS, PAD>(sm, a, s, P, gp);
+  else
+    direct_pairs<C, kDirectQ2Items<EPT>, 2, COLS, PAD>(sm, a, s, P, gp);
 }
 
 // The stages are grouped by radix in the fixed order of kRadixOrder (the
@@ -226,10 +314,10 @@ __device__ __noinline__ void run_direct_stage(C* sm, const PassArgs& a, const St
 // register allocation of each butterfly size separate (mixing sizes inside
 // one loop body makes the allocator spill).  POW2 kernels carry only the
 // power-of-two regions.
-template <typename C, int EPT, bool COLS, bool POW2, bool PAD>
+template <typename C, int EPT, bool COLS, bool POW2, bool PAD, bool TCK>
 __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ tw) {
   int i = 0;
-  constexpr bool kC64 = sizeof(C) == 8;
+  constexpr bool kC64 = sizeof(C) == 8 && TCK;  // TCK = false: no tensor-core code in the kernel
   uint32_t* tab32 = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(sm) + a.tc_off);
   uint32_t* tab16 = tab32 + (a.cnt[kTC32Region] ? tc_words<32>() : 0);
   if constexpr (kC64) {
@@ -242,7 +330,7 @@ __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ t
   }
   if constexpr (!POW2) {
     _Pragma("unroll 1") for (int q = 0; q < a.cnt[kDirectRegion]; ++q, ++i)
-        run_direct_stage<C, kDirectItems<EPT>, COLS, PAD>(sm, a, a.st[i], tw);
+        run_direct_stage<C, EPT, COLS, PAD>(sm, a, a.st[i], tw);
   }
 #define PFFT_REGION(RR, IDX)                                                     \
   _Pragma("unroll 1") for (int q = 0; q < a.cnt[IDX]; ++q, ++i)                  \
@@ -282,7 +370,7 @@ __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ t
 // The body takes the tile (blockIdx.x of a plain launch) and the signal index
 // (blockIdx.y) as arguments so that the grouped launches of many patterns
 // (batch_kernels.cu) run the same code on a per-CTA copy of the arguments.
-template <typename C, int EPT, bool POW2, bool PAD>
+template <typename C, int EPT, bool POW2, bool PAD, bool TCK = true>
 __device__ __forceinline__ void row_pass_body(const PassArgs& a, int tile, int sig, C* sm) {
   const C* __restrict__ tw = static_cast<const C*>(a.tw);
   const C* __restrict__ in = static_cast<const C*>(a.in) + (int64_t)sig * a.m;
@@ -327,7 +415,7 @@ __device__ __forceinline__ void row_pass_body(const PassArgs& a, int tile, int s
     if (sidx[k] >= 0) sm[phys<PAD>(sidx[k])] = (a.load_mode == MAP_WS) ? v[k] : maybe_conj(v[k], a.conj_in);
   }
   __syncthreads();
-  run_all_stages<C, EPT, false, POW2, PAD>(sm, a, tw);
+  run_all_stages<C, EPT, false, POW2, PAD, TCK>(sm, a, tw);
   using Rl = decltype(C::x);
   const Rl sc = Rl(a.scale);
 #pragma unroll
@@ -387,7 +475,7 @@ __device__ __forceinline__ int shear_index(const PassArgs& a, int j, const int* 
 // Column pass: all LB rows of T adjacent workspace columns per CTA, smem
 // layout [i][t].  The DFT runs over the (D-1) cycles inside the pencil.
 // Loads and stores are batched per thread as in the row pass.
-template <typename C, int EPT, bool POW2, bool PAD>
+template <typename C, int EPT, bool POW2, bool PAD, bool TCK = true>
 __device__ __forceinline__ void col_pass_body(const PassArgs& a, int tile, int sig, C* sm) {
   const C* __restrict__ tw = static_cast<const C*>(a.tw);
   const C* __restrict__ in = static_cast<const C*>(a.in) + (int64_t)sig * a.m;
@@ -435,7 +523,7 @@ __device__ __forceinline__ void col_pass_body(const PassArgs& a, int tile, int s
     if (sidx[k] >= 0) sm[phys<PAD>(sidx[k])] = maybe_conj(v[k], a.conj_in);
   }
   __syncthreads();
-  run_all_stages<C, EPT, true, POW2, PAD>(sm, a, tw);
+  run_all_stages<C, EPT, true, POW2, PAD, TCK>(sm, a, tw);
   using Rl = decltype(C::x);
   const Rl sc = Rl(a.scale);
   const bool ws_out = a.store_mode == MAP_WS;

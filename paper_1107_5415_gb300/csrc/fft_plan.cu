@@ -79,6 +79,37 @@ void set_box(BoxDesc& B, const IMat& H) {
 // Stages of a Stockham DFT along one pencil axis of length a and stride
 // sigma, in the radix order of kRadixOrder (Ns accumulates in that order);
 // twiddles come from a table of order nD (a multiple of a).
+// Smallest primitive root of the prime p (g^((p-1)/f) != 1 for every prime f | p - 1).
+int primitive_root(int p) {
+  std::vector<int> fs;
+  int n = p - 1;
+  for (int f = 2; f * f <= n; ++f)
+    if (n % f == 0) {
+      fs.push_back(f);
+      while (n % f == 0) n /= f;
+    }
+  if (n > 1) fs.push_back(n);
+  auto powmod = [p](int b, int e) {
+    long long r = 1, x = b;
+    while (e) {
+      if (e & 1) r = r * x % p;
+      x = x * x % p;
+      e >>= 1;
+    }
+    return int(r);
+  };
+  for (int g = 2; g < p; ++g) {
+    bool ok = true;
+    for (int f : fs)
+      if (powmod(g, (p - 1) / f) == 1) {
+        ok = false;
+        break;
+      }
+    if (ok) return g;
+  }
+  return 0;
+}
+
 bool axis_stages(std::vector<StageDesc>& out, int a, int sigma, int nD, bool tc) {
   std::vector<int> rad;
   if (!factor_radices(a, rad, tc)) return false;
@@ -92,6 +123,7 @@ bool axis_stages(std::vector<StageDesc>& out, int a, int sigma, int nD, bool tc)
     s.sigma = sigma;
     s.Ns = Ns;
     s.twstep = nD / (Ns * R);
+    s.gen = R >= kMinDirectRadix ? primitive_root(R) : 0;
     s.div_aR.init(uint32_t(s.aR));
     s.div_sigma.init(uint32_t(sigma));
     s.div_Ns.init(uint32_t(Ns));
@@ -139,10 +171,14 @@ int threads_for(const PassArgs& p, int ept) {
   int need = (p.T * p.L + ept - 1) / ept;
   for (int i = 0; i < p.nstages; ++i) {
     const int R = p.st[i].R;
-    if (radix_region(R) == kDirectRegion) {  // (R + 1) / 2 output pairs per butterfly
-      const int items = p.T * (p.L / R) * ((R + 1) / 2);
-      const int cap = ept / 2 + 2;  // kDirectItems
-      need = std::max(need, (items + cap - 1) / cap);
+    if (radix_region(R) == kDirectRegion) {  // the phases of run_direct_stage
+      const int nbfly = p.T * (p.L / R), h = (R - 1) / 2;
+      const int Q = R >= kDirectQ4MinRadix ? 4 : 2;
+      const int cap_main = ept / 8 + (Q == 4 ? 1 : 2);  // kDirectQ4Items / kDirectQ2Items
+      const int items = nbfly * ((h + Q - 1) / Q);
+      need = std::max(need, (nbfly * h + ept / 2 - 1) / (ept / 2));  // kDirectPre
+      need = std::max(need, (items + cap_main - 1) / cap_main);
+      need = std::max(need, (nbfly + kDirectZero - 1) / kDirectZero);
       continue;
     }
     const int nb = std::max(1, ept / R);
@@ -236,7 +272,8 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
     if (radix_region(p.st[i].R) == kDirectRegion) rmax = std::max(rmax, p.st[i].R);
   p.pad = rmax ? 0 : 1;
   p.dir_off = p.pad ? (nel - 1) + ((nel - 1) >> 4) + 1 : nel;
-  p.smem_bytes = int(size_t(p.dir_off + rmax) * elem_bytes(P.dtype));
+  // direct-stage tables: omega_R^{g^t} (R - 1 complex) and g^t (R - 1 int), with slack
+  p.smem_bytes = int(size_t(p.dir_off + 2 * rmax) * elem_bytes(P.dtype));
   p.tc = P.tc ? 1 : 0;
   p.tc_off = (p.smem_bytes + 15) & ~15;
   if (p.tc) {  // fragment tables of the radix-32 / 16 tensor-core stages (fft_tc.cuh)

@@ -41,11 +41,19 @@ constexpr int kDirectRegion = 7;
 constexpr int kTC32Region = 8;
 constexpr int kMinDirectRadix = 11;
 constexpr int kMaxDirectRadix = 1021;
-// Output pairs a thread holds in a direct stage: a butterfly of radix R >= 11
-// has (R + 1) / 2 <= 6R / 11 pairs, so EPT / 2 + 2 covers a tile of EPT
-// elements per thread.
+// Work items a thread holds in the phases of a direct stage (run_direct_stage),
+// for tiles of at most EPT points per thread: pre-pass pairs (h R' per
+// butterfly, h = (R - 1) / 2: at most EPT / 2), output items of 4 outputs
+// (R >= kDirectQ4MinRadix) or 2 outputs, and butterflies for y_0 (at most
+// EPT / 11 + 1).  The planner's thread count guarantees them.
+constexpr int kDirectQ4MinRadix = 37;
+constexpr int kDirectZero = 3;
 template <int EPT>
-constexpr int kDirectItems = EPT / 2 + 2;
+constexpr int kDirectPre = EPT / 2;
+template <int EPT>
+constexpr int kDirectQ4Items = EPT / 8 + 1;
+template <int EPT>
+constexpr int kDirectQ2Items = EPT / 8 + 2;
 
 // One radix stage of a Stockham autosort DFT along one axis of a pencil.
 struct StageDesc {
@@ -55,6 +63,7 @@ struct StageDesc {
   int sigma;   // stride of the axis inside the pencil (elements)
   int Ns;      // product of the radices of the earlier stages on this axis
   int twstep;  // tw_n / (Ns * R): index step into the pass's omega_{tw_n} table
+  int gen;     // direct stages: a primitive root of the prime R
   FastDiv div_aR, div_sigma, div_Ns;
 };
 
