@@ -219,6 +219,29 @@ pfft_status pwt_adjoint(pwt_plan p, const void* scaling, const void* const* wave
 
 pfft_status pwt_plan_destroy(pwt_plan p);
 
+/* General split step (Section 5.3, step 4) for a dilation J of any
+ * determinant p = |det J| <= 16 whose group G(J^T) = Z^d / J^T Z^d is cyclic
+ * (one elementary divisor of J above 1), with the p symbols supplied by the
+ * caller (step 1 of the algorithm computes them from the generating
+ * functions; the paper defines Dirichlet-type symbols only for |det J| = 2).
+ * M = J N must hold with N integral.  For every g in G(N^T) (box of H(N^T))
+ * and its fibre h_t = g + t N^T l (t < p, l a generator of G(J^T)):
+ *     parts[j][b][g] = p^{-1/2} sum_t conj(symbols[j][h_t]) c_hat[b][h_t],  j < p.
+ * symbols: device [p][|det M|] on the box of H(M^T); c_hat: device
+ * [batch][|det M|]; parts: device [p][batch][|det M| / p].  Plan-free: the
+ * exact setup runs on the host per call, the kernel is queued on `stream`.
+ * Errors: PFFT_ERR_NOT_INTEGRAL (J^{-1} M), PFFT_ERR_UNSUPPORTED (p > 16 or
+ * G(J^T) not cyclic), PFFT_ERR_OVERFLOW (|det M| >= 2^30), and the argument
+ * errors of pfft_plan_create. */
+pfft_status pwt_split_general(int d, const int64_t* M, const int64_t* J, int64_t batch, int dtype,
+                              const void* symbols, const void* c_hat, void* parts, void* stream);
+
+/* Adjoint of pwt_split_general: c_hat[b][h_t] = p^{-1/2} sum_j symbols[j][h_t]
+ * parts[j][b][g].  It inverts pwt_split_general when the matrix
+ * (symbols[j][h_t] / sqrt(p))_{j,t} is unitary on every fibre. */
+pfft_status pwt_merge_general(int d, const int64_t* M, const int64_t* J, int64_t batch, int dtype,
+                              const void* symbols, const void* parts, void* c_hat, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batches of many patterns of uneven size (serving-style mixes).
  *

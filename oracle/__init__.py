@@ -14,6 +14,9 @@ What it computes (each function cites the passage it follows):
                            ``pattern_oracle.c``; PARITY UNPINNED for its values).
   * ``wavelet_cascade``  : the dyadic repetition of Section 5.3 (input of the
                            next level = scaling part of this one).
+  * ``split_general``    : Section 5.3 step 4 for any |det J| = p with cyclic
+                           G(J^T), symbols given by the caller (and its adjoint
+                           ``merge_general``).
   * ``lattice``          : exact integer HNF / SNF / box enumeration.
 """
 from __future__ import annotations
@@ -266,3 +269,55 @@ def scaling_symbol(M, J, hs, symbol=DIRICHLET, eta=0.125):
     _load().po_scaling_symbol(d, adjMT[1], L.det(M), Ja[1], adjJT[1], L.det(J), int(symbol), float(eta),
                               len(hs), hp, _f64(out))
     return out
+
+
+def cyclic_generator_JT(J):
+    """A generator l of G(J^T) = Z^d / J^T Z^d when that group is cyclic
+    (one elementary divisor of J above 1): with J^T = Q E R (Smith form), the
+    class of Q e_d generates Z^d / Q E Z^d = Z^d / J^T Z^d."""
+    JT = L.transpose(J)
+    Q, E, R = L.snf(JT)
+    d = len(J)
+    if sum(1 for i in range(d) if abs(E[i][i]) > 1) > 1:
+        raise ValueError("G(J^T) is not cyclic")
+    return [Q[i][d - 1] for i in range(d)]
+
+
+def _general_fibres(M, J):
+    """Slots (box of H(M^T)) of the fibres h_t = g + t N^T l, t < p, for every
+    slot g of the box of H(N^T); Section 5.3 step 4 sums over these."""
+    N = exact_N(M, J)
+    p = abs(L.det(J))
+    HM, HN = L.hnf(L.transpose(M)), L.hnf(L.transpose(N))
+    shift = L.matvec(L.transpose(N), cyclic_generator_JT(J))
+    n = abs(L.det(N))
+    S = np.empty((n, p), dtype=np.int64)
+    for gs in range(n):
+        g = L.point_of(HN, gs)
+        for t in range(p):
+            S[gs, t] = L.slot_of(HM, L.box_reduce(HM, [a + t * b for a, b in zip(g, shift)]))
+    return S, p, n
+
+
+def split_general(M, J, symbols, c_hat):
+    """d_j[g] = p^{-1/2} sum_t conj(b_j(h_t)) c(h_t) (Section 5.3 step 4, with
+    the conjugated analysis symbols of this project's reading), for symbols
+    b_j given on the box of H(M^T): symbols [p, m], c_hat [batch, m] ->
+    parts [p, batch, m / p]."""
+    S, p, n = _general_fibres(M, J)
+    sym = np.asarray(symbols, dtype=np.complex128)
+    c = np.atleast_2d(np.asarray(c_hat, dtype=np.complex128))
+    return np.einsum("jnt,bnt->jbn", np.conj(sym[:, S]), c[:, S]) / np.sqrt(p)
+
+
+def merge_general(M, J, symbols, parts):
+    """Adjoint of ``split_general``: c(h_t) = p^{-1/2} sum_j b_j(h_t) d_j[g]."""
+    S, p, n = _general_fibres(M, J)
+    sym = np.asarray(symbols, dtype=np.complex128)
+    dp = np.asarray(parts, dtype=np.complex128)
+    batch = dp.shape[1]
+    c = np.zeros((batch, n * p), dtype=np.complex128)
+    vals = np.einsum("jnt,jbn->bnt", sym[:, S], dp) / np.sqrt(p)
+    for t in range(p):
+        c[:, S[:, t]] = vals[:, :, t]
+    return c

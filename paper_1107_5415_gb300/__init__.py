@@ -24,7 +24,7 @@ from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_C64, PFFT_C12
                     PFFT_MAP_INPUT_BOX,
                     PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_OUTPUT_SNF, PWT_DIRICHLET, PWT_DLVP,
                     PfftError, pfft_batch_create, pfft_batch_destroy, pfft_batch_forward, pfft_batch_info,
-                    pfft_batch_schedule, pfft_device_index_map,
+                    pfft_batch_schedule, pfft_device_index_map, pwt_merge_general, pwt_split_general,
                     pfft_forward, pfft_hermite_normal_form, pfft_index_map, pfft_inverse, pfft_plan_create,
                     pfft_last_device_status, pfft_plan_destroy, pfft_plan_info, pfft_profile_enable, pfft_profile_read,
                     pfft_smith_normal_form, pwt_adjoint, pwt_decompose, pwt_plan_create, pwt_plan_destroy,
@@ -33,7 +33,8 @@ from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_C64, PFFT_C12
 __all__ = [
     "PatternFFT", "WaveletSplit", "PatternBatch", "pattern_fft", "pattern_ifft", "wavelet_decompose",
     "PFFT_BATCH_NO_GRAPH", "PFFT_BATCH_AUTOTUNE", "PFFT_FLAG_TC_SPLIT", "pfft_batch_create", "pfft_batch_info",
-    "pfft_batch_schedule", "pfft_batch_forward", "pfft_batch_destroy",
+    "pfft_batch_schedule", "pfft_batch_forward", "pfft_batch_destroy", "split_general", "merge_general",
+    "pwt_split_general", "pwt_merge_general",
     "PfftError", "PFFT_C64", "PFFT_C128", "PWT_DIRICHLET", "PWT_DLVP",
     "PFFT_MAP_INPUT_BOX", "PFFT_MAP_OUTPUT_BOX", "PFFT_MAP_INPUT_SNF", "PFFT_MAP_OUTPUT_SNF",
     "pfft_plan_create", "pfft_plan_info", "pfft_index_map", "pfft_device_index_map", "pfft_forward",
@@ -273,6 +274,31 @@ class PatternBatch:
             self.close()
         except Exception:
             pass
+
+
+def split_general(M, J, symbols: torch.Tensor, c_hat: torch.Tensor, stream=None) -> torch.Tensor:
+    """Section 5.3 step 4 for |det J| = p (cyclic G(J^T)) with caller symbols
+    [p, |det M|]: c_hat [batch, |det M|] -> parts [p, batch, |det M| / p]."""
+    p, m = symbols.shape
+    batch = c_hat.shape[0]
+    _check_tensor(symbols, c_hat.dtype, (p, m), "symbols")
+    _check_tensor(c_hat, c_hat.dtype, (batch, m), "c_hat")
+    out = torch.empty((p, batch, m // p), dtype=c_hat.dtype, device=c_hat.device)
+    pwt_split_general(M, J, batch, _dtype_code(c_hat.dtype), symbols.data_ptr(), c_hat.data_ptr(), out.data_ptr(),
+                      _stream(stream))
+    return out
+
+
+def merge_general(M, J, symbols: torch.Tensor, parts: torch.Tensor, stream=None) -> torch.Tensor:
+    """Adjoint of ``split_general`` (its inverse for unitary symbol systems)."""
+    p, batch, n = parts.shape
+    m = symbols.shape[1]
+    _check_tensor(symbols, parts.dtype, (p, m), "symbols")
+    _check_tensor(parts, parts.dtype, (p, batch, n), "parts")
+    out = torch.empty((batch, m), dtype=parts.dtype, device=parts.device)
+    pwt_merge_general(M, J, batch, _dtype_code(parts.dtype), symbols.data_ptr(), parts.data_ptr(), out.data_ptr(),
+                      _stream(stream))
+    return out
 
 
 class _SplitFn(torch.autograd.Function):

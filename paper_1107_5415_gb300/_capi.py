@@ -79,6 +79,10 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_int)]),
     "pfft_batch_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pfft_batch_destroy": (ctypes.c_int, [_vp]),
+    "pwt_split_general": (ctypes.c_int, [ctypes.c_int, _i64p, _i64p, ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp,
+                                         _vp]),
+    "pwt_merge_general": (ctypes.c_int, [ctypes.c_int, _i64p, _i64p, ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp,
+                                         _vp]),
 }
 
 
@@ -302,3 +306,24 @@ def pfft_batch_forward(batch, in_ptr: int, c_hat_ptr: int, scaling_ptr, wavelet_
 
 def pfft_batch_destroy(batch):
     _check(lib().pfft_batch_destroy(batch), "pfft_batch_destroy")
+
+
+# ------------------------------------------------------------ general split step
+def _mj(M, J):
+    d, (a, p) = _mat(M)
+    dj, (b, q) = _mat(J)
+    if dj != d:
+        raise ValueError("M and J must have the same size")
+    return d, a, p, b, q
+
+
+def pwt_split_general(M, J, batch: int, dtype: int, symbols_ptr: int, c_hat_ptr: int, parts_ptr: int, stream: int):
+    d, a, p, b, q = _mj(M, J)
+    _check(lib().pwt_split_general(d, p, q, int(batch), int(dtype), symbols_ptr, c_hat_ptr, parts_ptr, stream),
+           "pwt_split_general")
+
+
+def pwt_merge_general(M, J, batch: int, dtype: int, symbols_ptr: int, parts_ptr: int, c_hat_ptr: int, stream: int):
+    d, a, p, b, q = _mj(M, J)
+    _check(lib().pwt_merge_general(d, p, q, int(batch), int(dtype), symbols_ptr, parts_ptr, c_hat_ptr, stream),
+           "pwt_merge_general")

@@ -426,3 +426,83 @@ def test_theorem3_dimension_step(seed):
     dM = sum(e > 1 for e in L.elementary_divisors(M))
     dN = sum(e > 1 for e in L.elementary_divisors(N))
     assert dM - dN in (0, 1)
+
+
+# ------------------------------------------- general split step (|det J| = p)
+GENERAL = [([[6, 1], [0, 9]], [[1, 0], [0, 3]]),            # p = 3, coordinate dilation
+           ([[10, 5], [5, 15]], [[1, 1], [-1, 4]]),         # p = 5, not triangular
+           ([[8, 4], [0, 12]], [[2, 0], [0, 1]]),           # p = 2
+           ([[4, 1, 0], [0, 6, 2], [0, 0, 7]], [[1, 0, 0], [0, 1, 0], [0, 0, 7]]),  # p = 7, d = 3
+           ([[12, 4], [4, 12]], [[1, 1], [-1, 3]])]         # p = 4 (cyclic G(J^T))
+
+
+@pytest.mark.parametrize("M,J", GENERAL)
+def test_general_fibres_partition_the_classes(M, J):
+    """The fibres of step 4: every class of G(M^T) lies in exactly one fibre,
+    and h_t - g lies in N^T Z^d with the p members pairwise different mod M^T Z^d."""
+    N = oracle.exact_N(M, J)
+    S, p, n = oracle._general_fibres(M, J)
+    m = abs(L.det(M))
+    assert p == abs(L.det(J)) and n * p == m
+    assert sorted(S.reshape(-1).tolist()) == list(range(m))
+    HM, HN = L.hnf(L.transpose(M)), L.hnf(L.transpose(N))
+    NTinv = L.inverse(L.transpose(N))
+    for gs in range(0, n, max(1, n // 17)):
+        g = L.point_of(HN, gs)
+        for t in range(p):
+            h = L.point_of(HM, int(S[gs, t]))
+            assert all(x.denominator == 1 for x in L.matvec(NTinv, [a - b for a, b in zip(h, g)]))
+
+
+def _dft_symbols(M, J):
+    """A unitary symbol system: b_j(h_t) = exp(-2 pi i j t / p) on the fibre
+    position t of every class (the columns of the p-point DFT)."""
+    S, p, n = oracle._general_fibres(M, J)
+    sym = np.zeros((p, n * p), dtype=np.complex128)
+    for t in range(p):
+        for j in range(p):
+            sym[j, S[:, t]] = np.exp(-2j * np.pi * j * t / p)
+    return sym
+
+
+@pytest.mark.parametrize("M,J", GENERAL)
+def test_general_split_unitary_symbols(M, J):
+    """With a unitary symbol system the split preserves the norm and the
+    adjoint undoes it; with b_0 = sqrt(p) on one fibre member and 0 elsewhere
+    the first part picks that member."""
+    m = abs(L.det(M))
+    c = _rand_c(m, 2, 11)
+    sym = _dft_symbols(M, J)
+    parts = oracle.split_general(M, J, sym, c)
+    assert np.allclose((np.abs(parts) ** 2).sum(axis=(0, 2)), (np.abs(c) ** 2).sum(axis=1), rtol=1e-13)
+    assert np.allclose(oracle.merge_general(M, J, sym, parts), c, atol=1e-12)
+    S, p, n = oracle._general_fibres(M, J)
+    pick = np.zeros((1, m), dtype=np.complex128)
+    pick[0, S[:, 0]] = np.sqrt(p)
+    assert np.allclose(oracle.split_general(M, J, pick, c)[0], c[:, S[:, 0]], atol=1e-13)
+
+
+@pytest.mark.parametrize("M,J", [([[8, 8], [-8, 8]], SI.J_DIAG_A), ([[6, 2], [-2, 6]], SI.J_DIAG_A),
+                                 ([[8, 0], [0, 8]], [[2, 0], [0, 1]])])
+def test_general_split_reduces_to_dirichlet_level(M, J):
+    """p = 2 with the Dirichlet symbol system (scaling A, wavelet
+    B(h) = A(h + N^T l) exp(-2 pi i h^T M^{-1} (J z))) gives the split of the
+    dedicated C routine."""
+    m = abs(L.det(M))
+    HM = L.hnf(L.transpose(M))
+    hs = np.array(list(L.box_points(HM)))
+    N = oracle.exact_N(M, J)
+    l1 = oracle.nonzero_class_JT(J)
+    NTl1 = L.matvec(L.transpose(N), l1)
+    A = oracle.scaling_symbol(M, J, hs, oracle.DIRICHLET)
+    shifted = np.array([L.box_reduce(HM, [a + b for a, b in zip(h, NTl1)]) for h in hs.tolist()])
+    A1 = oracle.scaling_symbol(M, J, shifted, oracle.DIRICHLET)
+    u = oracle.wavelet_shift(J)
+    Minv = L.inverse(M)
+    ph = np.array([float(sum(Fraction(int(h[i])) * sum(Minv[i][k] * u[k] for k in range(len(u)))
+                             for i in range(len(u))) % 1) for h in hs])
+    B = A1 * np.exp(-2j * np.pi * ph)
+    c = _rand_c(m, 2, 5)
+    parts = oracle.split_general(M, J, np.stack([A, B]), c)
+    d1, d2 = oracle.wavelet_level(M, J, oracle.DIRICHLET, c_hat=c)
+    assert np.allclose(parts[0], d1, atol=1e-12) and np.allclose(parts[1], d2, atol=1e-12)
