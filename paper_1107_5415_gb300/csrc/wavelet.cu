@@ -63,22 +63,21 @@ template <typename C, bool SMALL>
 static void launch_split_t(const LevelDesc& L, int batch, int mode, const void* cin, void* cout,
                            const void* d1in, const void* d2in, void* d1out, void* d2out, cudaStream_t s) {
   const int blk = 256;
-  long long gx = (L.mN + blk - 1) / blk;
-  const long long cap = (152LL * 16 + batch - 1) / batch;  // about 16 resident waves of CTAs in total
-  if (gx > cap) gx = cap;
-  if (gx < 1) gx = 1;
-  dim3 grid((unsigned)gx, (unsigned)batch);
+  unsigned gx, gy;
+  int chunk;
+  split_grid(L.mN, batch, gx, gy, chunk);
+  dim3 grid(gx, gy);
   auto c = [](const void* p) { return static_cast<const C*>(p); };
   auto m = [](void* p) { return static_cast<C*>(p); };
   if (mode == 0)
-    split_kernel<C, 0, true, SMALL><<<grid, blk, 0, s>>>(L, batch, c(cin), nullptr, nullptr, nullptr, m(d1out),
-                                                          m(d2out));
+    split_kernel<C, 0, true, SMALL><<<grid, blk, 0, s>>>(L, batch, chunk, c(cin), nullptr, nullptr, nullptr,
+                                                          m(d1out), m(d2out));
   else if (mode == 1)
-    split_kernel<C, 1, true, SMALL><<<grid, blk, 0, s>>>(L, batch, nullptr, m(cout), c(d1in), c(d2in), nullptr,
-                                                          nullptr);
+    split_kernel<C, 1, true, SMALL><<<grid, blk, 0, s>>>(L, batch, chunk, nullptr, m(cout), c(d1in), c(d2in),
+                                                          nullptr, nullptr);
   else
-    split_kernel<C, 2, true, SMALL><<<grid, blk, 0, s>>>(L, batch, nullptr, m(cout), c(d1in), c(d2in), nullptr,
-                                                          nullptr);
+    split_kernel<C, 2, true, SMALL><<<grid, blk, 0, s>>>(L, batch, chunk, nullptr, m(cout), c(d1in), c(d2in),
+                                                          nullptr, nullptr);
 }
 
 template <typename C>
@@ -545,17 +544,18 @@ extern "C" pfft_status pwt_decompose_noalloc(int d, const int64_t* M, int levels
   for (int l = 0; l < levels; ++l) {
     void* d1 = (l == levels - 1) ? scaling : static_cast<void*>(scratch + (l & 1) * half);
     const LevelDesc& L = P.lv[l];
-    long long gx = (L.mN + 255) / 256;
-    const long long cap = (152LL * 16 + batch - 1) / batch;
-    if (gx > cap) gx = cap;
-    dim3 grid(unsigned(gx < 1 ? 1 : gx), unsigned(batch));
+    unsigned gx, gy;
+    int chunk;
+    split_grid(L.mN, int(batch), gx, gy, chunk);
+    dim3 grid(gx, gy);
     const float2* src = static_cast<const float2*>(cur);
     float2* o1 = static_cast<float2*>(d1);
     float2* o2 = static_cast<float2*>(wavelets[l]);
     if (L.small)
-      split_kernel<float2, 0, false, true><<<grid, 256, 0, s>>>(L, int(batch), src, nullptr, nullptr, nullptr, o1, o2);
+      split_kernel<float2, 0, false, true><<<grid, 256, 0, s>>>(L, int(batch), chunk, src, nullptr, nullptr, nullptr, o1,
+                                                                o2);
     else
-      split_kernel<float2, 0, false, false><<<grid, 256, 0, s>>>(L, int(batch), src, nullptr, nullptr, nullptr, o1,
+      split_kernel<float2, 0, false, false><<<grid, 256, 0, s>>>(L, int(batch), chunk, src, nullptr, nullptr, nullptr, o1,
                                                                   o2);
     if (cudaGetLastError() != cudaSuccess) return PFFT_ERR_CUDA;
     cur = d1;

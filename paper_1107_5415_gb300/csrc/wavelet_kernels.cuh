@@ -127,9 +127,11 @@ __device__ __forceinline__ C wavelet_phase(const LevelDesc& L, const int* h) {
 }
 
 // mode 0: decompose c -> (d1, d2); 1: reconstruct; 2: adjoint, for the
-// fibre of slot gs of the box of H(N^T).  The pointers address one signal.
+// fibre of slot gs of the box of H(N^T) in each of `batch` signals (signal b
+// at c + b mM, d + b mN).  The symbols depend on the fibre only: they are
+// evaluated once and applied to every signal.
 template <typename C, int MODE, bool TAB, bool SMALL>
-__device__ __forceinline__ void split_fibre(const LevelDesc& L, int gs, const C* __restrict__ cin,
+__device__ __forceinline__ void split_fibre(const LevelDesc& L, int gs, int batch, const C* __restrict__ cin,
                                             C* __restrict__ cout, const C* __restrict__ d1in,
                                             const C* __restrict__ d2in, C* __restrict__ d1out,
                                             C* __restrict__ d2out) {
@@ -167,34 +169,59 @@ __device__ __forceinline__ void split_fibre(const LevelDesc& L, int gs, const C*
   // B(h0) = A(h1) e(h0), B(h1) = A(h0) e(h1), e(h1) = -e(h0)
   const C e0 = wavelet_phase<C, TAB, SMALL>(L, g);
   const Rl r2 = Rl(0.70710678118654752440);
+  const long long mM = L.mM, mN = L.mN;
   if (MODE == 0) {
-    const C c0 = cin[slot0], c1 = cin[slot1];
-    d1out[gs] = cscale(cadd(cscale(c0, A0), cscale(c1, A1)), r2);
-    // conj(B0) c0 + conj(B1) c1 = conj(e0) (A1 c0 - A0 c1)
-    d2out[gs] = cscale(cmul(cconj(e0), csub(cscale(c0, A1), cscale(c1, A0))), r2);
+    const C ce = cconj(e0);
+#pragma unroll 4
+    for (int b = 0; b < batch; ++b) {
+      const C c0 = cin[b * mM + slot0], c1 = cin[b * mM + slot1];
+      d1out[b * mN + gs] = cscale(cadd(cscale(c0, A0), cscale(c1, A1)), r2);
+      // conj(B0) c0 + conj(B1) c1 = conj(e0) (A1 c0 - A0 c1)
+      d2out[b * mN + gs] = cscale(cmul(ce, csub(cscale(c0, A1), cscale(c1, A0))), r2);
+    }
   } else {
-    const C a = d1in[gs], bb = d2in[gs];
     const Rl S = A0 * A0 + A1 * A1;
     const Rl fac = (MODE == 1) ? Rl(1.41421356237309504880) / S : r2;
-    const C eb = cmul(e0, bb);
-    cout[slot0] = cscale(cadd(cscale(a, A0), cscale(eb, A1)), fac);
-    cout[slot1] = cscale(csub(cscale(a, A1), cscale(eb, A0)), fac);
+#pragma unroll 4
+    for (int b = 0; b < batch; ++b) {
+      const C a = d1in[b * mN + gs], bb = d2in[b * mN + gs];
+      const C eb = cmul(e0, bb);
+      cout[b * mM + slot0] = cscale(cadd(cscale(a, A0), cscale(eb, A1)), fac);
+      cout[b * mM + slot1] = cscale(csub(cscale(a, A1), cscale(eb, A0)), fac);
+    }
   }
 }
 
-// One thread per fibre g (grid-stride over the slots of one signal,
-// blockIdx.y = signal).
+// One thread per fibre g (grid-stride over the slots of the box of H(N^T));
+// blockIdx.y takes the signals [y chunk, (y + 1) chunk) of the batch in turn
+// (one chunk holds the whole batch unless the level has few fibres).
 template <typename C, int MODE, bool TAB = true, bool SMALL = false>
-__global__ void __launch_bounds__(256) split_kernel(LevelDesc L, int batch, const C* __restrict__ cin,
+__global__ void __launch_bounds__(256) split_kernel(LevelDesc L, int batch, int chunk, const C* __restrict__ cin,
                                                     C* __restrict__ cout, const C* __restrict__ d1in,
                                                     const C* __restrict__ d2in, C* __restrict__ d1out,
                                                     C* __restrict__ d2out) {
-  (void)batch;
-  const long long oM = (long long)blockIdx.y * L.mM, oN = (long long)blockIdx.y * L.mN;
+  const int b0 = blockIdx.y * chunk;
+  const int nb = min(chunk, batch - b0);
+  if (nb <= 0) return;
+  const long long oM = (long long)b0 * L.mM, oN = (long long)b0 * L.mN;
   for (int gs = blockIdx.x * blockDim.x + threadIdx.x; gs < L.mN; gs += gridDim.x * blockDim.x)
-    split_fibre<C, MODE, TAB, SMALL>(L, gs, MODE == 0 ? cin + oM : nullptr, MODE == 0 ? nullptr : cout + oM,
+    split_fibre<C, MODE, TAB, SMALL>(L, gs, nb, MODE == 0 ? cin + oM : nullptr, MODE == 0 ? nullptr : cout + oM,
                                      MODE == 0 ? nullptr : d1in + oN, MODE == 0 ? nullptr : d2in + oN,
                                      MODE == 0 ? d1out + oN : nullptr, MODE == 0 ? d2out + oN : nullptr);
+}
+
+// Launch shape of split_kernel: enough fibre CTAs for about 8 resident waves,
+// and the signals split into chunks only when the fibres alone are too few.
+inline void split_grid(long long mN, int batch, unsigned& gx, unsigned& gy, int& chunk) {
+  long long x = (mN + 255) / 256;
+  if (x > 152LL * 8) x = 152LL * 8;
+  if (x < 1) x = 1;
+  long long y = (152LL * 8 + x - 1) / x;
+  if (y > batch) y = batch;
+  if (y < 1) y = 1;
+  chunk = int((batch + y - 1) / y);
+  gy = unsigned((batch + chunk - 1) / chunk);
+  gx = unsigned(x);
 }
 
 // Host: the descriptor of one split level of M by J (wavelet.cu).
