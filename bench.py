@@ -58,11 +58,18 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def source_hash():
+# sources that define each measured kernel and its launch configuration
+KERNEL_SOURCES = {
+    "row_pass": ["fft_tma.cuh", "fft_tma.cu", "fft_fast.cuh", "fft_plan.hpp", "device_common.cuh", "fft_plan.cu"],
+    "col_pass": ["fft_fast.cuh", "fft_fast_f32.cu", "fft_plan.hpp", "device_common.cuh", "fft_plan.cu"],
+}
+
+
+def source_hash(kernel):
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1107_5415_gb300", "csrc", "*"))):
-        with open(p, "rb") as f:
-            h.update(os.path.basename(p).encode())
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1107_5415_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -77,7 +84,7 @@ def recorded_traffic(kernel):
     except (OSError, ValueError):
         return None
     ent = rec.get(kernel)
-    if not ent or ent.get("source_hash") != source_hash():
+    if not ent or ent.get("source_hash") != source_hash(kernel):
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -356,14 +363,14 @@ def bench_directional(pf, torch, peaks_hbm, steps=20, warmup=3):
     return out
 
 
-def bench_mix(pf, torch, peaks_hbm, steps=10, warmup=3):
+def bench_mix(pf, torch, peaks_hbm, steps=10, warmup=3, n_patterns=None):
     """Uneven serving-style mix: 4096 seeded patterns (d in {2, 3}, upper
     triangular, diagonals in [16, 512], det <= 2^20 and even), forward
     transform + one Dirichlet split level per pattern (dilation from the
     pattern's parity), replayed as one CUDA graph with the autotuned schedule.
     Inputs: seeded complex normal values drawn on the device."""
     w = SI.WORKLOADS["uneven_mix"]
-    Ms = SI.uneven_mix(w["n_patterns"], seed=w["seed"], even_det=w["even_det"])
+    Ms = SI.uneven_mix(w["n_patterns"], seed=w["seed"], even_det=w["even_det"])[:n_patterns or w["n_patterns"]]
     Js = [SI.parity_dilation(M) for M in Ms]
     t0 = time.perf_counter()
     B = pf.PatternBatch(Ms, Js, pf.PWT_DIRICHLET, flags=pf.PFFT_BATCH_AUTOTUNE)
@@ -375,7 +382,7 @@ def bench_mix(pf, torch, peaks_hbm, steps=10, warmup=3):
     sc = torch.empty(B.total // 2, dtype=torch.complex64, device="cuda")
     wv = torch.empty_like(sc)
     stream = torch.cuda.current_stream()
-    out = {"workload": "uneven mix: 4096 patterns, forward FFT + one split level each", "patterns": B.n,
+    out = {"workload": f"uneven mix: {B.n} patterns, forward FFT + one split level each", "patterns": B.n,
            "points": int(B.total), "plan_s": t_plan, "schedule": dict(zip(("row_budget", "col_budget", "order"),
                                                                            B.schedule()))}
     for split, name in ((True, "fft_split"), (False, "fft_only")):
@@ -471,7 +478,7 @@ def run_native(args):
         plan.forward(x, y)
         tc = bench_tc(pf, torch, x, y, ms, peaks_hbm)
     wavelet = None if args.no_wavelet else bench_wavelet(pf, torch, peaks_hbm=peaks_hbm)
-    mix = None if args.no_mix else bench_mix(pf, torch, peaks_hbm=peaks_hbm)
+    mix = None if args.no_mix else bench_mix(pf, torch, peaks_hbm=peaks_hbm, n_patterns=args.mix_patterns)
     table1 = None if args.no_table1 else bench_table1(pf, torch, peaks_hbm)
     directional = None if args.no_directional else bench_directional(pf, torch, peaks_hbm)
     if args.no_e2e:
@@ -596,6 +603,8 @@ def main(argv=None):
     ap.add_argument("--no-wavelet", action="store_true", help="skip the wavelet cascade measurement")
     ap.add_argument("--no-mix", action="store_true", help="skip the uneven pattern-mix measurement")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core form measurement")
+    ap.add_argument("--mix-patterns", type=int, default=0,
+                    help="first N patterns of the uneven mix only (profiling runs; default all 4096)")
     ap.add_argument("--no-table1", action="store_true", help="skip the Table 1 pattern sweep")
     ap.add_argument("--no-directional", action="store_true", help="skip the directional dilation comparison")
     ap.add_argument("--batch", type=int, default=0, help="override the workload batch (profiling runs)")
