@@ -363,6 +363,26 @@ def bench_directional(pf, torch, peaks_hbm, steps=20, warmup=3):
     return out
 
 
+def bench_snf_layout(pf, torch, x, ms_box, steps=50, warmup=5):
+    """The same step in the Smith-coordinate layout (PFFT_FLAG_LAYOUT_SNF):
+    the transform without the gather from and the scatter to the Hermite
+    boxes (the order the paper computes in); its time against the box layout
+    shows what the reordering costs."""
+    w = SI.WORKLOADS[WORKLOAD]
+    plan = pf.PatternFFT(w["M"], x.shape[0], layout="snf")
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+
+    def step():
+        plan.forward(x, y)
+        plan.inverse(y, z)
+
+    ms = _time_ms(torch, step, steps, warmup)
+    plan.close()
+    return {"value": 2.0 * x.numel() / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
+            "box_layout_ms_per_step": ms_box, "box_over_snf": ms_box / ms}
+
+
 def bench_mix(pf, torch, peaks_hbm, steps=10, warmup=3, n_patterns=None):
     """Uneven serving-style mix: 4096 seeded patterns (d in {2, 3}, upper
     triangular, diagonals in [16, 512], det <= 2^20 and even), forward
@@ -477,6 +497,7 @@ def run_native(args):
     if not args.no_tc:
         plan.forward(x, y)
         tc = bench_tc(pf, torch, x, y, ms, peaks_hbm)
+    snf_layout = None if args.no_tc else bench_snf_layout(pf, torch, x, ms)
     wavelet = None if args.no_wavelet else bench_wavelet(pf, torch, peaks_hbm=peaks_hbm)
     mix = None if args.no_mix else bench_mix(pf, torch, peaks_hbm=peaks_hbm, n_patterns=args.mix_patterns)
     table1 = None if args.no_table1 else bench_table1(pf, torch, peaks_hbm)
@@ -486,7 +507,8 @@ def run_native(args):
         plan.close()
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "points/s", "ms_per_step": ms_max,
-                              "kernels": prof, "tc_split": tc, "wavelet": wavelet, "uneven_mix": mix,
+                              "kernels": prof, "tc_split": tc, "snf_layout": snf_layout, "wavelet": wavelet,
+                              "uneven_mix": mix,
                               "table1": table1, "directional": directional,
                               "note": "profiling run (no e2e)"}), flush=True)
         return 0
@@ -573,6 +595,7 @@ def run_native(args):
             "kernels": kernels,
             "cpu_baseline": cpu,
             "tc_split": tc,
+            "snf_layout": snf_layout,
             "wavelet": wavelet,
             "uneven_mix": mix,
             "table1": table1,

@@ -86,7 +86,17 @@ enum {
    * (three products per tile), which recovers fp32-level accuracy.  Values
    * entering those stages must stay below the fp16 range (|x| < 65504).
    * Without the flag every stage runs in plain fp32 on the CUDA cores. */
-  PFFT_FLAG_TC_SPLIT = 1u
+  PFFT_FLAG_TC_SPLIT = 1u,
+  /* Smith-coordinate layout (the reordering-free order of Section 4): the
+   * input is indexed by lambda = (lambda_1 .. lambda_d), lambda_j in
+   * [0, eps_j), row-major, and the output by mu the same way, where
+   * lambda(y) and mu(k) are the coordinates that pfft_index_map returns with
+   * PFFT_MAP_INPUT_SNF / PFFT_MAP_OUTPUT_SNF for a box-layout plan of the same
+   * M (cycles of length 1 contribute no index).  The transform is then the
+   * d-dimensional DFT of sizes eps_1 .. eps_d (Theorem 1) without any
+   * gather or scatter; the box extents reported by pfft_plan_info are the
+   * eps_j.  Requires eps_d < 2^24. */
+  PFFT_FLAG_LAYOUT_SNF = 2u
 };
 
 /* Which index map pfft_index_map returns. */
@@ -119,8 +129,9 @@ pfft_status pfft_smith_normal_form(int d, const int64_t* M, int64_t* Q, int64_t*
  * ------------------------------------------------------------------------- */
 
 /* Plan the transform on P(M) for `batch` signals of |det M| points each.
- * M: d*d row-major host array.  dtype: PFFT_C64 or PFFT_C128.  flags: 0 or
- * PFFT_FLAG_TC_SPLIT (PFFT_C64 only, else PFFT_ERR_UNSUPPORTED).
+ * M: d*d row-major host array.  dtype: PFFT_C64 or PFFT_C128.  flags: any of
+ * PFFT_FLAG_TC_SPLIT (PFFT_C64 only, else PFFT_ERR_UNSUPPORTED) and
+ * PFFT_FLAG_LAYOUT_SNF.
  * Computes H(M), H(M^T), the Smith form and the basis of Theorem 1
  * (Section 3, eqs. (basisPM), (basisGM); Remark 2 allows any biorthogonal
  * pair, and the planner picks the one whose longest cycle runs along the

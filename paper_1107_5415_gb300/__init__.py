@@ -20,7 +20,8 @@ import numpy as np
 import torch
 
 from . import _capi
-from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_C64, PFFT_C128, PFFT_FLAG_TC_SPLIT,
+from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_C64, PFFT_C128, PFFT_FLAG_LAYOUT_SNF,
+                    PFFT_FLAG_TC_SPLIT,
                     PFFT_MAP_INPUT_BOX,
                     PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_OUTPUT_SNF, PWT_DIRICHLET, PWT_DLVP,
                     PfftError, pfft_batch_create, pfft_batch_destroy, pfft_batch_forward, pfft_batch_info,
@@ -32,7 +33,7 @@ from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_C64, PFFT_C12
 
 __all__ = [
     "PatternFFT", "WaveletSplit", "PatternBatch", "pattern_fft", "pattern_ifft", "wavelet_decompose",
-    "PFFT_BATCH_NO_GRAPH", "PFFT_BATCH_AUTOTUNE", "PFFT_FLAG_TC_SPLIT", "pfft_batch_create", "pfft_batch_info",
+    "PFFT_BATCH_NO_GRAPH", "PFFT_BATCH_AUTOTUNE", "PFFT_FLAG_TC_SPLIT", "PFFT_FLAG_LAYOUT_SNF", "pfft_batch_create", "pfft_batch_info",
     "pfft_batch_schedule", "pfft_batch_forward", "pfft_batch_destroy", "split_general", "merge_general",
     "pwt_split_general", "pwt_merge_general",
     "PfftError", "PFFT_C64", "PFFT_C128", "PWT_DIRICHLET", "PWT_DLVP",
@@ -75,16 +76,21 @@ def _check_tensor(x: torch.Tensor, dtype, shape, name: str):
 class PatternFFT:
     """Plan of the transform on P(M) for ``batch`` signals (wraps pfft_plan)."""
 
-    def __init__(self, M, batch: int = 1, dtype=torch.complex64, tc_split: bool = False):
+    def __init__(self, M, batch: int = 1, dtype=torch.complex64, tc_split: bool = False, layout: str = "box"):
         """``tc_split``: run the radix-16 / 32 stages on the tensor cores in
-        split fp16 (PFFT_FLAG_TC_SPLIT; complex64 only)."""
+        split fp16 (PFFT_FLAG_TC_SPLIT; complex64 only).  ``layout``: "box"
+        (Hermite boxes, the default) or "snf" (Smith coordinates,
+        PFFT_FLAG_LAYOUT_SNF)."""
+        if layout not in ("box", "snf"):
+            raise ValueError('layout must be "box" or "snf"')
         self.M = np.asarray(M, dtype=np.int64)
         self.d = int(self.M.shape[0])
         self.batch = int(batch)
         self.dtype = dtype
         self.tc_split = bool(tc_split)
-        self._h = pfft_plan_create(self.M, self.batch, _dtype_code(dtype),
-                                   PFFT_FLAG_TC_SPLIT if tc_split else 0)
+        self.layout = layout
+        flags = (PFFT_FLAG_TC_SPLIT if tc_split else 0) | (PFFT_FLAG_LAYOUT_SNF if layout == "snf" else 0)
+        self._h = pfft_plan_create(self.M, self.batch, _dtype_code(dtype), flags)
         self.m, self.dM, self.eps, self.in_box, self.out_box = pfft_plan_info(self._h, self.d)
 
     @property

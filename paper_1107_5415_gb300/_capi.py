@@ -21,6 +21,7 @@ _lib = None
 
 PFFT_C64, PFFT_C128 = 0, 1
 PFFT_FLAG_TC_SPLIT = 1
+PFFT_FLAG_LAYOUT_SNF = 2
 PFFT_MAP_INPUT_BOX, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_SNF = 0, 1, 2, 3
 PWT_DIRICHLET, PWT_DLVP = 0, 1
 PFFT_BATCH_NO_GRAPH, PFFT_BATCH_AUTOTUNE = 1, 2

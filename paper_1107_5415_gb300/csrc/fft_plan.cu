@@ -762,7 +762,7 @@ static void release(pfft_plan_s* P) { plan_release(P); }
 extern "C" pfft_status pfft_plan_create(pfft_plan* out, int d, const int64_t* M, int64_t batch,
                                         int dtype, unsigned flags) {
   if (!out || !M || batch < 1 || batch > 65535 || (dtype != PFFT_C64 && dtype != PFFT_C128) ||
-      (flags & ~unsigned(PFFT_FLAG_TC_SPLIT)))
+      (flags & ~unsigned(PFFT_FLAG_TC_SPLIT | PFFT_FLAG_LAYOUT_SNF)) || d < 1 || d > 4)
     return PFFT_ERR_ARG;
   if ((flags & PFFT_FLAG_TC_SPLIT) && dtype != PFFT_C64) return PFFT_ERR_UNSUPPORTED;
   *out = nullptr;
@@ -776,7 +776,25 @@ extern "C" pfft_status pfft_plan_create(pfft_plan* out, int d, const int64_t* M,
   }
   pfft_status st;
   try {
-    st = plan_host(*P, d, M);
+    if (flags & PFFT_FLAG_LAYOUT_SNF) {
+      // Smith-coordinate layout: by Theorem 1 the transform of M in Smith
+      // coordinates is the plain d-dimensional DFT of sizes eps_1 .. eps_d,
+      // i.e. the transform of diag(eps) in the box layout, whose box order is
+      // the row-major order of lambda (input) and mu (output).
+      IMat A(d), Q, R, U, V;
+      std::vector<i64> eps;
+      for (int i = 0; i < d * d; ++i) {
+        if (M[i] >= (int64_t(1) << 24) || M[i] <= -(int64_t(1) << 24)) throw LatticeError{PFFT_ERR_OVERFLOW, "entry"};
+        A.a[i] = M[i];
+      }
+      if (determinant(A) == 0) throw LatticeError{PFFT_ERR_SINGULAR, "singular"};
+      smith_normal_form(A, Q, eps, R, U, V);
+      std::vector<int64_t> D(size_t(d) * d, 0);
+      for (int i = 0; i < d; ++i) D[size_t(i) * d + i] = eps[i];
+      st = plan_host(*P, d, D.data());
+    } else {
+      st = plan_host(*P, d, M);
+    }
     if (st == PFFT_OK && P->m * batch >= (int64_t(1) << 40)) st = PFFT_ERR_OVERFLOW;
     if (st == PFFT_OK) st = plan_device(*P);
   } catch (const LatticeError& e) {
