@@ -403,6 +403,9 @@ extern "C" pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, c
     P->arena = &B->arena;
     P->generic_only = true;
     P->own_workspace = false;
+    // grouped kernels: 16 complex64 points per thread (64 registers, two
+    // 512-thread CTAs per SM) to hide the latency of the table-driven passes
+    P->ept_c64 = kGroupedEptC64;
     pfft_status st;
     try {
       st = plan_host(*P, d[i], M + mo);

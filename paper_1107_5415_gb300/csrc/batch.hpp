@@ -9,6 +9,7 @@
 namespace pfft {
 
 constexpr int kSplitThreads = 256;
+constexpr int kGroupedEptC64 = 16;  // complex64 points per thread of the grouped pass kernels
 constexpr int kSplitPerThread = 4;  // fibres per thread of a grouped split CTA
 // Dynamic shared memory of a grouped pass CTA: the 227 KB per CTA less room
 // for the static copy of its pass descriptor.

@@ -32,8 +32,8 @@ __device__ __forceinline__ void copy_to_smem(T* dst, const T* src) {
   for (int i = threadIdx.x; i < int(sizeof(T) / 16); i += blockDim.x) d[i] = __ldg(s + i);
 }
 
-template <typename C, int EPT, bool COLS>
-__global__ void __launch_bounds__(kMaxThreads, 1) grouped_pass_kernel(GroupArgs g) {
+template <typename C, int EPT, bool COLS, int MINB>
+__global__ void __launch_bounds__(kMaxThreads, MINB) grouped_pass_kernel(GroupArgs g) {
   __shared__ PassArgs a;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int it = find_item(g.cta0, g.n, blockIdx.x);
@@ -96,12 +96,12 @@ int allow_smem(K* k) {
 
 int prepare_grouped(int dtype) {
   if (dtype == 0) {
-    static const int ok = allow_smem(grouped_pass_kernel<float2, 32, false>) |
-                          allow_smem(grouped_pass_kernel<float2, 32, true>);
+    static const int ok = allow_smem(grouped_pass_kernel<float2, kGroupedEptC64, false, 2>) |
+                          allow_smem(grouped_pass_kernel<float2, kGroupedEptC64, true, 2>);
     return ok;
   }
-  static const int ok = allow_smem(grouped_pass_kernel<double2, 16, false>) |
-                        allow_smem(grouped_pass_kernel<double2, 16, true>);
+  static const int ok = allow_smem(grouped_pass_kernel<double2, 16, false, 1>) |
+                        allow_smem(grouped_pass_kernel<double2, 16, true, 1>);
   return ok;
 }
 
@@ -111,14 +111,14 @@ int launch_grouped_pass(const GroupArgs& g, int cols, int dtype, int nctas, int 
   if (smem > kGroupedMaxDynSmem || threads > kMaxThreads) return -1;
   if (dtype == 0) {
     if (cols)
-      grouped_pass_kernel<float2, 32, true><<<nctas, threads, smem, s>>>(g);
+      grouped_pass_kernel<float2, kGroupedEptC64, true, 2><<<nctas, threads, smem, s>>>(g);
     else
-      grouped_pass_kernel<float2, 32, false><<<nctas, threads, smem, s>>>(g);
+      grouped_pass_kernel<float2, kGroupedEptC64, false, 2><<<nctas, threads, smem, s>>>(g);
   } else {
     if (cols)
-      grouped_pass_kernel<double2, 16, true><<<nctas, threads, smem, s>>>(g);
+      grouped_pass_kernel<double2, 16, true, 1><<<nctas, threads, smem, s>>>(g);
     else
-      grouped_pass_kernel<double2, 16, false><<<nctas, threads, smem, s>>>(g);
+      grouped_pass_kernel<double2, 16, false, 1><<<nctas, threads, smem, s>>>(g);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

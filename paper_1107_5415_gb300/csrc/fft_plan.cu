@@ -208,7 +208,7 @@ bool tile_fits(int L, int row_max, int ept) {
 }
 
 pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) {
-  const int ept = P.dtype == PFFT_C64 ? 32 : 16;
+  const int ept = P.dtype == PFFT_C64 ? P.ept_c64 : 16;
   p.cols = cols;
   p.nD = P.nD;
   p.LB = P.LB;
@@ -382,7 +382,7 @@ pfft_status pfft::plan_host(pfft_plan_s& P, int d, const int64_t* Mv) {
   // length-n_b DFTs (twiddle exp(-2 pi i lambda_a mu_b / n) between the passes)
   // and lambda_a becomes one more pencil axis of the column pass.
   const int row_max = P.dtype == PFFT_C64 ? 16384 : 8192;
-  const int ept = P.dtype == PFFT_C64 ? 32 : 16;
+  const int ept = P.dtype == PFFT_C64 ? P.ept_c64 : 16;
   if (P.fs_N > 1 && !tile_fits(int(std::min<i64>(P.fs_N, row_max + 1)), row_max, ept)) {
     const i64 other = P.m / P.fs_N;
     int best = 0;

@@ -32,6 +32,7 @@ struct pfft_plan_s {
   bool generic_only = false;     // shared-memory Stockham kernels only (grouped launches)
   bool own_workspace = true;     // allocate the LB x nD workspace
   bool tc = false;               // split-precision tensor-core radix-16 / 32 stages
+  int ept_c64 = 32;              // complex64 points per thread of the generic kernels
   // device state
   int device = 0;
   int* dtab = nullptr;
