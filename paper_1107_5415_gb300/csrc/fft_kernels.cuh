@@ -553,14 +553,16 @@ __device__ __forceinline__ void col_pass_body(const PassArgs& a, int tile, int s
   }
 }
 
-template <typename C, int EPT, bool POW2, bool PAD>
-__global__ void __launch_bounds__(kMaxThreads, 1) row_pass_kernel(PassArgs a) {
+// MINB: resident CTAs per SM the register allocation is fitted to (2 for the
+// 16-points-per-thread build, whose tiles hold at most 8192 points).
+template <typename C, int EPT, bool POW2, bool PAD, int MINB = 1>
+__global__ void __launch_bounds__(kMaxThreads, MINB) row_pass_kernel(PassArgs a) {
   extern __shared__ unsigned char smem_raw[];
   row_pass_body<C, EPT, POW2, PAD>(a, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
 }
 
-template <typename C, int EPT, bool POW2, bool PAD>
-__global__ void __launch_bounds__(kMaxThreads, 1) col_pass_kernel(PassArgs a) {
+template <typename C, int EPT, bool POW2, bool PAD, int MINB = 1>
+__global__ void __launch_bounds__(kMaxThreads, MINB) col_pass_kernel(PassArgs a) {
   extern __shared__ unsigned char smem_raw[];
   col_pass_body<C, EPT, POW2, PAD>(a, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
 }
@@ -574,23 +576,25 @@ inline int configure_kernel(const void* k) {
   return 0;
 }
 
-template <typename C, int EPT, bool POW2, bool PAD>
+template <typename C, int EPT, bool POW2, bool PAD, int MINB>
 inline int launch_typed_pad(const PassArgs& a, cudaStream_t s) {
   dim3 grid(a.groups, a.batch), block(a.nthreads);
-  static const int row_ok = configure_kernel(reinterpret_cast<const void*>(row_pass_kernel<C, EPT, POW2, PAD>));
-  static const int col_ok = configure_kernel(reinterpret_cast<const void*>(col_pass_kernel<C, EPT, POW2, PAD>));
+  static const int row_ok =
+      configure_kernel(reinterpret_cast<const void*>(row_pass_kernel<C, EPT, POW2, PAD, MINB>));
+  static const int col_ok =
+      configure_kernel(reinterpret_cast<const void*>(col_pass_kernel<C, EPT, POW2, PAD, MINB>));
   if (row_ok != 0 || col_ok != 0) return -1;
   if (a.cols)
-    col_pass_kernel<C, EPT, POW2, PAD><<<grid, block, a.smem_bytes, s>>>(a);
+    col_pass_kernel<C, EPT, POW2, PAD, MINB><<<grid, block, a.smem_bytes, s>>>(a);
   else
-    row_pass_kernel<C, EPT, POW2, PAD><<<grid, block, a.smem_bytes, s>>>(a);
+    row_pass_kernel<C, EPT, POW2, PAD, MINB><<<grid, block, a.smem_bytes, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <typename C, int EPT, bool POW2>
+template <typename C, int EPT, bool POW2, int MINB = 1>
 inline int launch_typed(const PassArgs& a, cudaStream_t s) {
-  if constexpr (POW2) return launch_typed_pad<C, EPT, true, true>(a, s);  // no direct stages
-  return a.pad ? launch_typed_pad<C, EPT, POW2, true>(a, s) : launch_typed_pad<C, EPT, POW2, false>(a, s);
+  if constexpr (POW2) return launch_typed_pad<C, EPT, true, true, MINB>(a, s);  // no direct stages
+  return a.pad ? launch_typed_pad<C, EPT, POW2, true, MINB>(a, s) : launch_typed_pad<C, EPT, POW2, false, MINB>(a, s);
 }
 
 }  // namespace pfft

@@ -3,6 +3,7 @@
 
 namespace pfft {
 int launch_pass_generic(const PassArgs& a, int dtype, cudaStream_t s) {
-  return dtype == 0 ? launch_typed<float2, 32, false>(a, s) : launch_typed<double2, 16, false>(a, s);
+  if (dtype != 0) return launch_typed<double2, 16, false>(a, s);
+  return a.ept == 16 ? launch_typed<float2, 16, false, 2>(a, s) : launch_typed<float2, 32, false>(a, s);
 }
 }  // namespace pfft

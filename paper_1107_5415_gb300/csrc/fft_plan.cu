@@ -263,7 +263,11 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
       p.fast = 0;
     }
   }
-  p.nthreads = threads_for(p, ept);
+  // generic kernels: 16 points per thread (64 registers, two CTAs per SM)
+  // when the tile fits 512 threads, else 32; the tensor-core stages need 32
+  p.ept = ept;
+  if (P.dtype == PFFT_C64 && !P.tc && ept == 32 && threads_for(p, 16) <= kMaxThreads) p.ept = 16;
+  p.nthreads = threads_for(p, p.ept);
   if (cols && T > 32) p.nthreads = (p.nthreads + T - 1) / T * T;  // each thread keeps one column
   if (p.nthreads > kMaxThreads) return PFFT_ERR_UNSUPPORTED;
   const int nel = T * p.L;

@@ -80,6 +80,7 @@ struct alignas(16) PassArgs {
   int tc_off;   // byte offset of the tensor-core fragment tables in shared memory
   int dir_off;  // shared-memory element offset of the omega_R table of a direct stage
   int pad;      // 1: padded shared-memory tile (x + x / 16); 0 when the pass has direct stages
+  int ept;      // points per thread of the generic kernels (16 or 32 for complex64, 16 for complex128)
   int pow2;     // all radices are powers of two
   int fast;       // 1: use the register-resident power-of-two kernels (fft_fast.cuh)
   int fast_tail;  // radix of the first stage (1 = none)
