@@ -191,6 +191,18 @@ pfft_status pfft_profile_read(pfft_plan p, const char** names, int64_t* launches
 
 enum { PWT_DIRICHLET = 0, PWT_DLVP = 1 };
 
+/* Flags of pwt_plan_create. */
+enum {
+  /* The coefficients on G(M^T) of the first level (the input of
+   * pwt_decompose, the output of pwt_reconstruct / pwt_adjoint) are in the
+   * Smith-coordinate order that a pfft plan of the same M created with
+   * PFFT_FLAG_LAYOUT_SNF writes (mu row-major over the cycles), so that a
+   * transform -> split pipeline runs without any reordering (the split in
+   * Smith coordinates of Section 5.3, Lemma 2).  All other parts keep the box
+   * layout. */
+  PWT_FLAG_INPUT_SNF = 1u
+};
+
 /* Plan `levels` split steps: level l (1-based) splits coefficients on
  * G(M_l^T) (M_1 = M) into a scaling part and a wavelet part on G(N_l^T),
  * N_l = J_l^{-1} M_l, and level l+1 splits the scaling part (M_{l+1} = N_l).
@@ -198,7 +210,7 @@ enum { PWT_DIRICHLET = 0, PWT_DLVP = 1 };
  *   symbol : PWT_DIRICHLET (Section 6.2) or PWT_DLVP (de la Vallee Poussin
  *            reading: sqrt|det J| times the periodised trapezoid of blend
  *            width eta, 0 < eta < 1; not defined in the paper)
- *   batch, dtype as for pfft_plan_create; flags: 0.
+ *   batch, dtype as for pfft_plan_create; flags: 0 or PWT_FLAG_INPUT_SNF.
  * Returns PFFT_ERR_NOT_INTEGRAL if some J_l^{-1} M_l is not integral. */
 pfft_status pwt_plan_create(pwt_plan* out, int d, const int64_t* M, int levels, const int64_t* J,
                             int symbol, double eta, int64_t batch, int dtype, unsigned flags);

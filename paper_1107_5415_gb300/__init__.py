@@ -24,6 +24,7 @@ from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_C64, PFFT_C12
                     PFFT_FLAG_TC_SPLIT,
                     PFFT_MAP_INPUT_BOX,
                     PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_OUTPUT_SNF, PWT_DIRICHLET, PWT_DLVP,
+                    PWT_FLAG_INPUT_SNF,
                     PfftError, pfft_batch_create, pfft_batch_destroy, pfft_batch_forward, pfft_batch_info,
                     pfft_batch_schedule, pfft_device_index_map, pwt_merge_general, pwt_split_general,
                     pfft_forward, pfft_hermite_normal_form, pfft_index_map, pfft_inverse, pfft_plan_create,
@@ -33,7 +34,7 @@ from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_C64, PFFT_C12
 
 __all__ = [
     "PatternFFT", "WaveletSplit", "PatternBatch", "pattern_fft", "pattern_ifft", "wavelet_decompose",
-    "PFFT_BATCH_NO_GRAPH", "PFFT_BATCH_AUTOTUNE", "PFFT_FLAG_TC_SPLIT", "PFFT_FLAG_LAYOUT_SNF", "pfft_batch_create", "pfft_batch_info",
+    "PFFT_BATCH_NO_GRAPH", "PFFT_BATCH_AUTOTUNE", "PFFT_FLAG_TC_SPLIT", "PFFT_FLAG_LAYOUT_SNF", "PWT_FLAG_INPUT_SNF", "pfft_batch_create", "pfft_batch_info",
     "pfft_batch_schedule", "pfft_batch_forward", "pfft_batch_destroy", "split_general", "merge_general",
     "pwt_split_general", "pwt_merge_general",
     "PfftError", "PFFT_C64", "PFFT_C128", "PWT_DIRICHLET", "PWT_DLVP",
@@ -177,14 +178,21 @@ class WaveletSplit:
     """Plan of ``levels`` split steps (wraps pwt_plan)."""
 
     def __init__(self, M, Js, symbol: int = PWT_DIRICHLET, eta: float = 0.125, batch: int = 1,
-                 dtype=torch.complex64):
+                 dtype=torch.complex64, input_layout: str = "box"):
+        """``input_layout``: "box" (default) or "snf" -- the first level's
+        coefficients in the Smith-coordinate order of a ``PatternFFT(M,
+        layout="snf")`` output (PWT_FLAG_INPUT_SNF)."""
+        if input_layout not in ("box", "snf"):
+            raise ValueError('input_layout must be "box" or "snf"')
         self.M = np.asarray(M, dtype=np.int64)
         self.d = int(self.M.shape[0])
         self.Js = np.asarray(Js, dtype=np.int64)
         self.levels = int(self.Js.shape[0])
         self.batch = int(batch)
         self.dtype = dtype
-        self._h = pwt_plan_create(self.M, self.Js, symbol, eta, self.batch, _dtype_code(dtype))
+        self.input_layout = input_layout
+        self._h = pwt_plan_create(self.M, self.Js, symbol, eta, self.batch, _dtype_code(dtype),
+                                  PWT_FLAG_INPUT_SNF if input_layout == "snf" else 0)
         self.sizes = []
         self.boxes = []
         for lev in range(self.levels + 1):

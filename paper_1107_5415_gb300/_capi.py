@@ -24,6 +24,7 @@ PFFT_FLAG_TC_SPLIT = 1
 PFFT_FLAG_LAYOUT_SNF = 2
 PFFT_MAP_INPUT_BOX, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_SNF = 0, 1, 2, 3
 PWT_DIRICHLET, PWT_DLVP = 0, 1
+PWT_FLAG_INPUT_SNF = 1
 PFFT_BATCH_NO_GRAPH, PFFT_BATCH_AUTOTUNE = 1, 2
 
 STATUS = {0: "PFFT_OK", 1: "PFFT_ERR_ARG", 2: "PFFT_ERR_SINGULAR", 3: "PFFT_ERR_OVERFLOW",

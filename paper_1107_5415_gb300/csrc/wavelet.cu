@@ -40,6 +40,7 @@
 #include "wavelet_kernels.cuh"
 #include "lattice.hpp"
 #include "plan_common.hpp"
+#include "plan_internal.hpp"
 
 namespace pfft {
 
@@ -315,6 +316,42 @@ static pfft_status plan_levels(pwt_plan_s& P, const int64_t* Mv, const int64_t* 
   return PFFT_OK;
 }
 
+// Smith-coordinate order of the first level's coefficients: the mu basis of
+// the transform planner for M (the order a PFFT_FLAG_LAYOUT_SNF plan of M
+// writes), and mu of N^T l1.
+static pfft_status set_snf_input(LevelDesc& L, int d, const int64_t* Mv, const int64_t* Jv) {
+  pfft_plan_s T;
+  pfft_status st = plan_host(T, d, Mv);
+  if (st != PFFT_OK) return st;
+  if (T.D > 4) return PFFT_ERR_UNSUPPORTED;
+  IMat M(d), J(d);
+  for (int i = 0; i < d * d; ++i) {
+    M.a[i] = Mv[i];
+    J.a[i] = Jv[i];
+  }
+  const i64 dJ = determinant(J);
+  IMat N = matmul(adjugate(J), M);
+  for (auto& x : N.a) x /= dJ;  // integral (checked by plan_levels)
+  std::vector<i64> l1;
+  if (!nonzero_class(J, l1)) return PFFT_ERR_UNSUPPORTED;
+  L.snf_D = T.D;
+  int str = 1;
+  for (int j = T.D - 1; j >= 0; --j) {
+    L.snf_n[j] = T.n[j];
+    L.snf_str[j] = str;
+    str *= T.n[j];
+    i128 acc = 0;
+    for (int c = 0; c < d; ++c) {
+      L.snf_mu[j][c] = posmod(T.MU[j][c], T.n[j]);
+      i64 v = 0;  // (N^T l1)_c
+      for (int k = 0; k < d; ++k) v += N(k, c) * l1[k];
+      acc += (i128)L.snf_mu[j][c] * v;
+    }
+    L.snf_l1[j] = int(posmod(i64(acc % T.n[j]), T.n[j]));
+  }
+  return PFFT_OK;
+}
+
 static pfft_status plan_device(pwt_plan_s& P) {
   const size_t cb = cbytes(P.dtype);
   size_t total = 0;
@@ -351,7 +388,8 @@ extern "C" pfft_status pwt_plan_create(pwt_plan* out, int d, const int64_t* M, i
                                        const int64_t* J, int symbol, double eta, int64_t batch,
                                        int dtype, unsigned flags) {
   if (!out || !M || !J || d < 1 || d > 4 || levels < 1 || levels > 64 || batch < 1 ||
-      batch > (int64_t(1) << 20) || (dtype != PFFT_C64 && dtype != PFFT_C128) || flags != 0 ||
+      batch > (int64_t(1) << 20) || (dtype != PFFT_C64 && dtype != PFFT_C128) ||
+      (flags & ~unsigned(PWT_FLAG_INPUT_SNF)) ||
       (symbol != PWT_DIRICHLET && symbol != PWT_DLVP) ||
       (symbol == PWT_DLVP && !(eta > 0.0 && eta < 1.0)))
     return PFFT_ERR_ARG;
@@ -368,6 +406,7 @@ extern "C" pfft_status pwt_plan_create(pwt_plan* out, int d, const int64_t* M, i
   try {
     st = plan_levels(*P, M, J);
     if (st == PFFT_OK && P->sizes[0] * batch >= (int64_t(1) << 40)) st = PFFT_ERR_OVERFLOW;
+    if (st == PFFT_OK && (flags & PWT_FLAG_INPUT_SNF)) st = set_snf_input(P->lv[0], d, M, J);
     if (st == PFFT_OK) st = plan_device(*P);
   } catch (const LatticeError& e) {
     st = pfft_status(e.code);

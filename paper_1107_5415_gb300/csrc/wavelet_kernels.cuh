@@ -43,6 +43,15 @@ struct LevelDesc {
   int offq;              // multiple of q that makes ph32 . h non-negative
   const void* tab_lo;    // exp(-2 pi i t / q), t < 2^kLoBits
   const void* tab_hi;    // exp(-2 pi i (t << kLoBits) / q)
+  // Smith-coordinate order of the coefficients on G(M^T) (first level of a
+  // plan created with PWT_FLAG_INPUT_SNF): the slot of h is the row-major
+  // index of mu(h) = (MU_j . h mod n_j) over the snf_D non-trivial cycles,
+  // and mu(h + N^T l1) = mu(h) + mu_l1 (mu is additive on G(M^T)).
+  int snf_D;             // 0: box order of H(M^T)
+  int snf_n[4];
+  int snf_str[4];
+  long long snf_mu[4][4];  // MU_j (reduced mod n_j), one row per cycle
+  int snf_l1[4];           // mu(N^T l1)
 };
 
 // Periodised weight w(N^{-T} h) of the point h (see the header comment);
@@ -156,6 +165,22 @@ __device__ __forceinline__ void split_fibre(const LevelDesc& L, int gs, int batc
 #pragma unroll
   for (int r = 0; r < 4; ++r)
     if (r < L.d) slot1 += h1[r] * L.HM.stride[r];
+  if (L.snf_D) {  // coefficients on G(M^T) in Smith-coordinate order
+    slot0 = slot1 = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (j >= L.snf_D) break;
+      long long acc = 0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < L.d) acc += L.snf_mu[j][c] * g[c];
+      const int mu0 = int(acc % L.snf_n[j]);
+      int mu1 = mu0 + L.snf_l1[j];
+      if (mu1 >= L.snf_n[j]) mu1 -= L.snf_n[j];
+      slot0 += mu0 * L.snf_str[j];
+      slot1 += mu1 * L.snf_str[j];
+    }
+  }
   const Rl w0 = fibre_weight<Rl, SMALL>(L, g);
   const Rl w1 = Rl(1) - w0;
   Rl A0, A1;
