@@ -403,7 +403,7 @@ def bench_mix(pf, torch, peaks_hbm, steps=10, warmup=3, n_patterns=None):
     wv = torch.empty_like(sc)
     stream = torch.cuda.current_stream()
     out = {"workload": f"uneven mix: {B.n} patterns, forward FFT + one split level each", "patterns": B.n,
-           "points": int(B.total), "plan_s": t_plan, "schedule": dict(zip(("row_budget", "col_budget", "order"),
+           "points": int(B.total), "plan_s": t_plan, "schedule": dict(zip(("row_budget", "col_budget", "order", "max_radix"),
                                                                            B.schedule()))}
     for split, name in ((True, "fft_split"), (False, "fft_only")):
         for _ in range(warmup):

@@ -287,7 +287,8 @@ pfft_status pwt_merge_general(int d, const int64_t* M, const int64_t* J, int64_t
  * ------------------------------------------------------------------------- */
 enum {
   PFFT_BATCH_NO_GRAPH = 1u, /* queue the grouped launches directly instead of replaying a graph */
-  PFFT_BATCH_AUTOTUNE = 2u  /* time candidate tile schedules at creation and keep the fastest */
+  PFFT_BATCH_AUTOTUNE = 2u, /* time candidate tile / radix schedules at creation and keep the fastest */
+  PFFT_BATCH_RADIX8 = 4u    /* start from radix-8 power-of-two stages instead of radix 16 */
 };
 
 /* n >= 1 patterns; d: host array of n dimensions (1..4); M: host array, the
@@ -304,9 +305,10 @@ pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, const int64_
 /* m: host array of n (|det M_i|) or NULL; total: sum of m_i or NULL. */
 pfft_status pfft_batch_info(pfft_batch b, int64_t* m, int64_t* total);
 
-/* The chosen schedule: element budgets of the row- and column-pass tiles and
- * the launch order (1: largest work first, 0: pattern order).  NULLs allowed. */
-pfft_status pfft_batch_schedule(pfft_batch b, int* row_budget, int* col_budget, int* order);
+/* The chosen schedule: element budgets of the row- and column-pass tiles, the
+ * launch order (1: largest work first, 0: pattern order) and the largest
+ * power-of-two radix of the stages (16 or 8).  NULLs allowed. */
+pfft_status pfft_batch_schedule(pfft_batch b, int* row_budget, int* col_budget, int* order, int* max_radix);
 
 /* in -> c_hat for every pattern; if the batch has dilations and scaling and
  * wavelet are non-NULL, also c_hat -> (scaling, wavelet).  Device pointers,

@@ -20,7 +20,7 @@ import numpy as np
 import torch
 
 from . import _capi
-from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_C64, PFFT_C128, PFFT_FLAG_LAYOUT_SNF,
+from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_BATCH_RADIX8, PFFT_C64, PFFT_C128, PFFT_FLAG_LAYOUT_SNF,
                     PFFT_FLAG_TC_SPLIT,
                     PFFT_MAP_INPUT_BOX,
                     PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_OUTPUT_SNF, PWT_DIRICHLET, PWT_DLVP,
@@ -34,7 +34,7 @@ from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_C64, PFFT_C12
 
 __all__ = [
     "PatternFFT", "WaveletSplit", "PatternBatch", "pattern_fft", "pattern_ifft", "wavelet_decompose",
-    "PFFT_BATCH_NO_GRAPH", "PFFT_BATCH_AUTOTUNE", "PFFT_FLAG_TC_SPLIT", "PFFT_FLAG_LAYOUT_SNF", "PWT_FLAG_INPUT_SNF", "pfft_batch_create", "pfft_batch_info",
+    "PFFT_BATCH_NO_GRAPH", "PFFT_BATCH_AUTOTUNE", "PFFT_BATCH_RADIX8", "PFFT_FLAG_TC_SPLIT", "PFFT_FLAG_LAYOUT_SNF", "PWT_FLAG_INPUT_SNF", "pfft_batch_create", "pfft_batch_info",
     "pfft_batch_schedule", "pfft_batch_forward", "pfft_batch_destroy", "split_general", "merge_general",
     "pwt_split_general", "pwt_merge_general",
     "PfftError", "PFFT_C64", "PFFT_C128", "PWT_DIRICHLET", "PWT_DLVP",
@@ -254,7 +254,7 @@ class PatternBatch:
         self.offsets = np.concatenate([[0], np.cumsum(self.m)[:-1]]).astype(np.int64)
 
     def schedule(self):
-        """(row tile budget, column tile budget, order) chosen at creation."""
+        """(row tile budget, column tile budget, order, largest power-of-two radix) chosen at creation."""
         return pfft_batch_schedule(self._h)
 
     def forward(self, x: torch.Tensor, c_hat=None, scaling=None, wavelet=None, split: bool = True, stream=None):

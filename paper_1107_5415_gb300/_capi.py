@@ -25,7 +25,7 @@ PFFT_FLAG_LAYOUT_SNF = 2
 PFFT_MAP_INPUT_BOX, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_SNF = 0, 1, 2, 3
 PWT_DIRICHLET, PWT_DLVP = 0, 1
 PWT_FLAG_INPUT_SNF = 1
-PFFT_BATCH_NO_GRAPH, PFFT_BATCH_AUTOTUNE = 1, 2
+PFFT_BATCH_NO_GRAPH, PFFT_BATCH_AUTOTUNE, PFFT_BATCH_RADIX8 = 1, 2, 4
 
 STATUS = {0: "PFFT_OK", 1: "PFFT_ERR_ARG", 2: "PFFT_ERR_SINGULAR", 3: "PFFT_ERR_OVERFLOW",
           4: "PFFT_ERR_NOT_INTEGRAL", 5: "PFFT_ERR_UNSUPPORTED", 6: "PFFT_ERR_OOM", 7: "PFFT_ERR_CUDA",
@@ -78,7 +78,7 @@ _SIGS = {
                                          _i64p, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_uint]),
     "pfft_batch_info": (ctypes.c_int, [_vp, _i64p, _i64p]),
     "pfft_batch_schedule": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                           ctypes.POINTER(ctypes.c_int)]),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "pfft_batch_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "pfft_batch_destroy": (ctypes.c_int, [_vp]),
     "pwt_split_general": (ctypes.c_int, [ctypes.c_int, _i64p, _i64p, ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp,
@@ -295,10 +295,10 @@ def pfft_batch_info(batch, n: int):
 
 
 def pfft_batch_schedule(batch):
-    r, c, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(lib().pfft_batch_schedule(batch, ctypes.byref(r), ctypes.byref(c), ctypes.byref(o)),
+    r, c, o, x = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().pfft_batch_schedule(batch, ctypes.byref(r), ctypes.byref(c), ctypes.byref(o), ctypes.byref(x)),
            "pfft_batch_schedule")
-    return r.value, c.value, o.value
+    return r.value, c.value, o.value, x.value
 
 
 def pfft_batch_forward(batch, in_ptr: int, c_hat_ptr: int, scaling_ptr, wavelet_ptr, stream: int):

@@ -48,7 +48,7 @@ struct pfft_batch_s {
   void* ws = nullptr;
   void* sched = nullptr;  // device: items and first-CTA tables of all launches
   std::vector<Bucket> rows, cols, splits;
-  int row_budget = 8192, col_budget = 8192, order = 1;
+  int row_budget = 8192, col_budget = 8192, order = 1, max2 = 16;
   std::vector<int> ident;  // patterns with m = 1 (the transform is a copy)
   cudaStream_t cap = nullptr;
   std::vector<cudaStream_t> streams;
@@ -125,7 +125,7 @@ pfft_status build_schedule(pfft_batch_s& B) {
   for (int i = 0; i < B.n; ++i) {
     pfft_plan_s* P = B.plans[i];
     if (P->D == 0) continue;
-    pfft_status st = plan_retile(*P, B.row_budget, B.col_budget);
+    pfft_status st = plan_retile(*P, B.row_budget, B.col_budget, B.max2);
     if (st != PFFT_OK) return st;
     const double scale = 1.0 / std::sqrt(double(P->m));
     const uintptr_t boff = uintptr_t(B.off[i]) * eb;
@@ -320,7 +320,8 @@ pfft_status time_schedule(pfft_batch_s& B, const void* in, void* chat, void* sc,
   return st;
 }
 
-// Coordinate search over the row budget, the column budget and the order.
+// Coordinate search over the row budget, the column budget, the launch order
+// and the largest power-of-two radix (16 or 8).
 pfft_status autotune(pfft_batch_s& B) {
   const size_t eb = ebytes(B.dtype);
   void *in = nullptr, *chat = nullptr, *sc = nullptr, *wv = nullptr;
@@ -339,11 +340,12 @@ pfft_status autotune(pfft_batch_s& B) {
   if (cudaMemset(in, 0, size_t(B.total) * eb) != cudaSuccess) return fail(PFFT_ERR_CUDA);
   const int budgets[] = {2048, 4096, 8192, 16384};
   float best = 1e30f;
-  int br = B.row_budget, bc = B.col_budget, bo = B.order;
-  auto trial = [&](int r, int c, int o) -> pfft_status {
+  int br = B.row_budget, bc = B.col_budget, bo = B.order, bx = B.max2;
+  auto trial = [&](int r, int c, int o, int x) -> pfft_status {
     B.row_budget = r;
     B.col_budget = c;
     B.order = o;
+    B.max2 = x;
     pfft_status e = build_schedule(B);
     if (e != PFFT_OK) return e;
     float ms = 0;
@@ -354,17 +356,20 @@ pfft_status autotune(pfft_batch_s& B) {
       br = r;
       bc = c;
       bo = o;
+      bx = x;
     }
     return PFFT_OK;
   };
   for (int r : budgets)
-    if ((st = trial(r, bc, bo)) != PFFT_OK) return fail(st);
+    if ((st = trial(r, bc, bo, bx)) != PFFT_OK) return fail(st);
   for (int c : budgets)
-    if ((st = trial(br, c, bo)) != PFFT_OK) return fail(st);
-  if ((st = trial(br, bc, 1 - bo)) != PFFT_OK) return fail(st);
+    if ((st = trial(br, c, bo, bx)) != PFFT_OK) return fail(st);
+  if ((st = trial(br, bc, 1 - bo, bx)) != PFFT_OK) return fail(st);
+  if ((st = trial(br, bc, bo, bx == 16 ? 8 : 16)) != PFFT_OK) return fail(st);
   B.row_budget = br;
   B.col_budget = bc;
   B.order = bo;
+  B.max2 = bx;
   st = build_schedule(B);
   return fail(st);
 }
@@ -374,7 +379,7 @@ pfft_status autotune(pfft_batch_s& B) {
 extern "C" pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, const int64_t* M, const int64_t* J,
                                          int symbol, double eta, int dtype, unsigned flags) {
   if (!out || n < 1 || !d || !M || (dtype != PFFT_C64 && dtype != PFFT_C128) ||
-      (flags & ~unsigned(PFFT_BATCH_NO_GRAPH | PFFT_BATCH_AUTOTUNE)))
+      (flags & ~unsigned(PFFT_BATCH_NO_GRAPH | PFFT_BATCH_AUTOTUNE | PFFT_BATCH_RADIX8)))
     return PFFT_ERR_ARG;
   if (J && (symbol != PWT_DIRICHLET && symbol != PWT_DLVP)) return PFFT_ERR_ARG;
   if (J && symbol == PWT_DLVP && !(eta > 0.0 && eta < 1.0)) return PFFT_ERR_ARG;
@@ -386,6 +391,7 @@ extern "C" pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, c
   B->n = n;
   B->dtype = dtype;
   B->flags = flags;
+  if (flags & PFFT_BATCH_RADIX8) B->max2 = 8;
   B->has_split = J != nullptr;
   auto fail = [&](pfft_status st) {
     delete B;
@@ -458,11 +464,13 @@ extern "C" pfft_status pfft_batch_info(pfft_batch b, int64_t* m, int64_t* total)
   return PFFT_OK;
 }
 
-extern "C" pfft_status pfft_batch_schedule(pfft_batch b, int* row_budget, int* col_budget, int* order) {
+extern "C" pfft_status pfft_batch_schedule(pfft_batch b, int* row_budget, int* col_budget, int* order,
+                                           int* max_radix) {
   if (!b) return PFFT_ERR_ARG;
   if (row_budget) *row_budget = b->row_budget;
   if (col_budget) *col_budget = b->col_budget;
   if (order) *order = b->order;
+  if (max_radix) *max_radix = b->max2;
   return PFFT_OK;
 }
 

@@ -24,7 +24,9 @@ namespace {
 // kMaxDirectRadix), then 16s, the rest of the power of two and 3, 5, 7 -- the
 // execution order of the stage regions.  Returns false if a prime factor is
 // not supported.
-bool factor_radices(int n, std::vector<int>& out, bool tc = false) {
+// max2: the largest power-of-two radix (16, or 8 for the schedules the batch
+// autotuner may pick instead).
+bool factor_radices(int n, std::vector<int>& out, bool tc = false, int max2 = 16) {
   out.clear();
   for (int p = kMinDirectRadix; p <= kMaxDirectRadix && p <= n; p += 2) {
     bool prime = true;
@@ -48,11 +50,14 @@ bool factor_radices(int n, std::vector<int>& out, bool tc = false) {
     out.push_back(32);
     p2 -= 5;
   }
-  while (p2 >= 4) {
+  while (max2 >= 16 && p2 >= 4) {
     out.push_back(16);
     p2 -= 4;
   }
-  if (p2 == 3) out.push_back(8);
+  while (p2 >= 3) {
+    out.push_back(8);
+    p2 -= 3;
+  }
   if (p2 == 2) out.push_back(4);
   if (p2 == 1) out.push_back(2);
   static const int primes[] = {3, 5, 7};
@@ -110,9 +115,9 @@ int primitive_root(int p) {
   return 0;
 }
 
-bool axis_stages(std::vector<StageDesc>& out, int a, int sigma, int nD, bool tc) {
+bool axis_stages(std::vector<StageDesc>& out, int a, int sigma, int nD, bool tc, int max2) {
   std::vector<int> rad;
-  if (!factor_radices(a, rad, tc)) return false;
+  if (!factor_radices(a, rad, tc, max2)) return false;
   int Ns = 1;
   for (int R : rad) {
     StageDesc s;
@@ -219,13 +224,13 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
   std::vector<StageDesc> stg;
   if (!cols) {
     p.L = P.nD;
-    if (!axis_stages(stg, P.nD, 1, P.nD, P.tc)) return PFFT_ERR_UNSUPPORTED;
+    if (!axis_stages(stg, P.nD, 1, P.nD, P.tc, P.max2)) return PFFT_ERR_UNSUPPORTED;
     p.groups = (P.LB + T - 1) / T;
   } else {
     p.L = P.LB;
     int sigma = 1;
     for (int s = int(P.pen.size()) - 1; s >= 0; --s) {  // pencil axes, last fastest
-      if (!axis_stages(stg, P.pen[s], sigma, p.tw_n, P.tc)) return PFFT_ERR_UNSUPPORTED;
+      if (!axis_stages(stg, P.pen[s], sigma, p.tw_n, P.tc, P.max2)) return PFFT_ERR_UNSUPPORTED;
       sigma *= P.pen[s];
     }
     p.groups = (P.nD + T - 1) / T;
@@ -746,8 +751,9 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
   return PFFT_OK;
 }
 
-pfft_status pfft::plan_retile(pfft_plan_s& P, int row_budget, int col_budget) {
-  if (!P.generic_only || P.D == 0) return PFFT_ERR_ARG;
+pfft_status pfft::plan_retile(pfft_plan_s& P, int row_budget, int col_budget, int max2) {
+  if (!P.generic_only || P.D == 0 || (max2 != 16 && max2 != 8)) return PFFT_ERR_ARG;
+  P.max2 = max2;
   pfft_status st = choose_and_configure(P.rowp, P, false, 64, std::max(row_budget, P.nD));
   if (st != PFFT_OK || P.pen.empty()) return st;
   return choose_and_configure(P.colp, P, true, 512, std::max(col_budget, P.LB));

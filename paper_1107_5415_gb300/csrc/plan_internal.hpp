@@ -33,6 +33,7 @@ struct pfft_plan_s {
   bool own_workspace = true;     // allocate the LB x nD workspace
   bool tc = false;               // split-precision tensor-core radix-16 / 32 stages
   int ept_c64 = 32;              // complex64 points per thread of the generic kernels
+  int max2 = 16;                 // largest power-of-two radix of the generic kernels (16 or 8)
   // device state
   int device = 0;
   int* dtab = nullptr;
@@ -54,7 +55,8 @@ pfft_status plan_host(pfft_plan_s& P, int d, const int64_t* M);
 // Device tables and pass descriptors.
 pfft_status plan_device(pfft_plan_s& P);
 // Re-choose the tiles of both passes (pencils per CTA) under the given
-// element budgets; generic kernels only.  Tables are unchanged.
-pfft_status plan_retile(pfft_plan_s& P, int row_budget, int col_budget);
+// element budgets and the largest power-of-two radix (16 or 8); generic
+// kernels only.  Tables are unchanged.
+pfft_status plan_retile(pfft_plan_s& P, int row_budget, int col_budget, int max2);
 void plan_release(pfft_plan_s* P);
 }  // namespace pfft

@@ -68,6 +68,24 @@ def test_small_mix_full(symbol):
         assert rel_l2(wv[h], d2[0]) <= 1e-5, (i, M)
 
 
+def test_radix8_schedule_full():
+    """The schedule with radix-8 power-of-two stages (one the autotuner may
+    pick), every output of a small mix with large power-of-two factors."""
+    Ms = _small_mix(80) + [[[256, 3], [0, 64]], [[128, 0, 0], [0, 8, 1], [0, 0, 4]]]
+    Js = [SI.parity_dilation(M) for M in Ms]
+    B = pf.PatternBatch(Ms, Js, pf.PWT_DIRICHLET, flags=pf.PFFT_BATCH_RADIX8)
+    assert B.schedule()[3] == 8
+    x = SI.complex_normal_flat(B.total, 81)
+    chat, sc, wv = (_np(t) for t in B.forward(torch.from_numpy(x).cuda()))
+    for i, (M, J) in enumerate(zip(Ms, Js)):
+        o, m = int(B.offsets[i]), int(B.m[i])
+        ref = oracle.pattern_fft(M, x[None, o:o + m])
+        assert rel_l2(chat[o:o + m], ref[0]) <= 1e-5, (i, M)
+        d1, d2 = oracle.wavelet_level(M, J, pf.PWT_DIRICHLET, c_hat=ref)
+        assert rel_l2(sc[o // 2:(o + m) // 2], d1[0]) <= 1e-5
+        assert rel_l2(wv[o // 2:(o + m) // 2], d2[0]) <= 1e-5
+
+
 def test_small_mix_complex128():
     Ms = _small_mix(50)
     Js = [SI.parity_dilation(M) for M in Ms]
@@ -116,8 +134,9 @@ def test_graph_direct_and_autotuned_schedules_agree():
     c = Bt.forward(x)
     for u, v in zip(a, c):
         assert rel_l2(_np(u), _np(v)) <= 1e-6
-    rb, cb, order = Bt.schedule()
+    rb, cb, order, radix = Bt.schedule()
     assert rb in (2048, 4096, 8192, 16384) and cb in (2048, 4096, 8192, 16384) and order in (0, 1)
+    assert radix in (8, 16)
 
 
 def test_batch_errors():
