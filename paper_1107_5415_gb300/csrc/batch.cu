@@ -430,6 +430,9 @@ extern "C" pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, c
       std::memset(&it, 0, sizeof(it));
       st = describe_split_level(d[i], M + mo, J + mo, symbol, eta, &it.L);
       if (st != PFFT_OK) return fail(st);
+      void* tab = nullptr;  // phase tables in the arena, as single plans have them
+      if (int e = B->arena.alloc(&tab, split_table_elems(it.L) * ebytes(dtype))) return fail(pfft_status(e));
+      if (launch_split_tables(it.L, tab, dtype) != 0) return fail(PFFT_ERR_CUDA);
       it.in_off = B->off[i];
       it.out_off = B->off[i] / 2;
       B->sitems.push_back(it);
@@ -437,6 +440,7 @@ extern "C" pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, c
     mo += size_t(d[i]) * d[i];
   }
   if (B->total >= (int64_t(1) << 40)) return fail(PFFT_ERR_OVERFLOW);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(PFFT_ERR_CUDA);  // tables built
   if (need_ws)
     if (int e = device_alloc(&B->ws, size_t(B->total) * ebytes(dtype))) return fail(pfft_status(e));
   if (cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(PFFT_ERR_CUDA);

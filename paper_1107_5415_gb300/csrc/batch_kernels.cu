@@ -77,9 +77,9 @@ __global__ void __launch_bounds__(kSplitThreads) grouped_split_kernel(const Spli
     const int gs = g0 + f * kSplitThreads;
     if (gs >= it.L.mN) break;
     if (it.L.small)
-      split_fibre<C, 0, false, true>(it.L, gs, 1, cin, nullptr, nullptr, nullptr, d1, d2);
+      split_fibre<C, 0, true, true>(it.L, gs, 1, cin, nullptr, nullptr, nullptr, d1, d2);
     else
-      split_fibre<C, 0, false, false>(it.L, gs, 1, cin, nullptr, nullptr, nullptr, d1, d2);
+      split_fibre<C, 0, true, false>(it.L, gs, 1, cin, nullptr, nullptr, nullptr, d1, d2);
   }
 }
 

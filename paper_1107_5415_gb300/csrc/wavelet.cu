@@ -483,8 +483,29 @@ extern "C" pfft_status pwt_adjoint(pwt_plan p, const void* scaling, const void* 
   return synthesise(p, scaling, wavelets, c_hat, stream, 2);
 }
 
-// Descriptor of one split level of M by J (host only; for batch plans, whose
-// kernels evaluate the phases without tables).
+// Two-level phase table of a level descriptor (lo: 2^kLoBits entries, then
+// hi: ceil(q / 2^kLoBits)) at `tab`, sized by split_table_elems; queued on the
+// legacy stream.
+size_t pfft::split_table_elems(const LevelDesc& L) {
+  return size_t(1 << kLoBits) + size_t((L.q + (1LL << kLoBits) - 1) >> kLoBits);
+}
+
+int pfft::launch_split_tables(LevelDesc& L, void* tab, int dtype) {
+  const int nhi = int((L.q + (1LL << kLoBits) - 1) >> kLoBits);
+  const size_t cb = dtype == PFFT_C64 ? 8 : 16;
+  L.tab_lo = tab;
+  L.tab_hi = static_cast<char*>(tab) + size_t(1 << kLoBits) * cb;
+  const int n = std::max(1 << kLoBits, nhi);
+  const int blk = 256, grd = (n + blk - 1) / blk;
+  if (dtype == PFFT_C64)
+    phase_table_kernel<float2><<<grd, blk>>>((float2*)L.tab_lo, (float2*)L.tab_hi, L.q, nhi);
+  else
+    phase_table_kernel<double2><<<grd, blk>>>((double2*)L.tab_lo, (double2*)L.tab_hi, L.q, nhi);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Descriptor of one split level of M by J (host only; batch plans add the
+// phase tables with launch_split_tables).
 pfft_status pfft::describe_split_level(int d, const int64_t* M, const int64_t* J, int symbol, double eta,
                                        LevelDesc* out) {
   if (!M || !J || !out || d < 1 || d > 4 || (symbol != PWT_DIRICHLET && symbol != PWT_DLVP) ||

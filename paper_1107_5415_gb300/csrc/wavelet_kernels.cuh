@@ -249,6 +249,11 @@ inline void split_grid(long long mN, int batch, unsigned& gx, unsigned& gy, int&
   gx = unsigned(x);
 }
 
+// Host (wavelet.cu): elements of the two-level phase table of a level, and its
+// construction at `tab` (sets tab_lo / tab_hi; 0 on success).
+size_t split_table_elems(const LevelDesc& L);
+int launch_split_tables(LevelDesc& L, void* tab, int dtype);
+
 // Host: the descriptor of one split level of M by J (wavelet.cu).
 pfft_status describe_split_level(int d, const int64_t* M, const int64_t* J, int symbol, double eta,
                                  LevelDesc* out);
