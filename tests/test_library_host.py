@@ -119,6 +119,23 @@ def test_batch_argument_errors():
         pf.pfft_batch_create([[[2, 0], [0, 2]]], [[[2, 0], [0, 1]], [[2, 0], [0, 1]]])
 
 
+def test_general_split_host_errors():
+    """Argument and lattice checks of the general split run on the host before
+    anything is queued (the device pointers are never touched here)."""
+    fake = 1 << 20  # never dereferenced: every call below fails on the host
+    cases = [([[4, 0], [0, 4]], [[2, 0], [0, 2]], 5),    # G(J^T) = Z_2 x Z_2 is not cyclic
+             ([[4, 0], [0, 4]], [[3, 0], [0, 1]], 4),    # J^{-1} M not integral
+             ([[17, 0], [0, 2]], [[17, 0], [0, 1]], 5),  # p = 17 > 16
+             ([[4, 0], [0, 4]], [[0, 0], [0, 1]], 2)]    # singular J
+    for M, J, code in cases:
+        with pytest.raises(pf.PfftError) as e:
+            pf.pwt_split_general(M, J, 1, pf.PFFT_C64, fake, fake + 64, fake + 128, 0)
+        assert e.value.status == code, (M, J)
+    with pytest.raises(pf.PfftError) as e:
+        pf.pwt_merge_general([[4, 0], [0, 4]], [[2, 0], [0, 1]], 1, pf.PFFT_C64, fake, fake, fake, 0)
+    assert e.value.status == 1  # parts and c_hat must differ
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_parity_dilation_divides_pattern(seed):
     """The workload helper that picks a dilation for each pattern of the
