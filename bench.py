@@ -613,6 +613,7 @@ def run_native(args):
             "directional": directional,
             "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": int(x.numel() * 8),
                     "d2h_bytes_per_step": int(z.numel() * 8),
+                    "ms_per_step": e2e_ms, "h2d_gbs": x.numel() * 8 / (e2e_ms * 1e-3) / 1e9,
                     "note": "pinned host buffers; uploads, transforms and downloads pipelined on three streams"},
             "gpu_launches": 4 * args.steps,
             "clocks": clk.summary(),
