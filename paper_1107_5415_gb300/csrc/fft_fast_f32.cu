@@ -4,6 +4,8 @@
 
 namespace pfft {
 
+int launch_col_ct_f32(const PassArgs& a, cudaStream_t s);  // fft_fast_ct.cu
+
 template <int DIM>
 static int launch_dim(const PassArgs& a, cudaStream_t s) {
   static const int row_ok = configure_kernel(reinterpret_cast<const void*>(row_fast_kernel<float2, 32, DIM>));
@@ -18,6 +20,10 @@ static int launch_dim(const PassArgs& a, cudaStream_t s) {
 }
 
 int launch_fast_f32(const PassArgs& a, cudaStream_t s) {
+  if (a.cols) {
+    const int rc = launch_col_ct_f32(a, s);
+    if (rc != -2) return rc;
+  }
   switch (a.d) {
     case 1: return launch_dim<1>(a, s);
     case 2: return launch_dim<2>(a, s);
