@@ -60,7 +60,8 @@ def measured_peaks():
 
 # sources that define each measured kernel and its launch configuration
 KERNEL_SOURCES = {
-    "row_pass": ["fft_tma.cuh", "fft_tma.cu", "fft_fast.cuh", "device_common.cuh"],
+    "row_pass": ["fft_tma.cuh", "fft_tma.cu", "fft_tma_ct.cuh", "fft_fast_ct.cuh", "fft_fast.cuh",
+                 "device_common.cuh"],
     "col_pass": ["fft_fast.cuh", "fft_fast_f32.cu", "fft_fast_ct.cuh", "fft_fast_ct.cu", "device_common.cuh"],
 }
 

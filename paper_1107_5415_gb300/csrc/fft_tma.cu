@@ -1,6 +1,9 @@
-// Instantiation of the bulk-copy staged row pass (fft_tma.cuh).
+// Instantiation of the bulk-copy staged row pass (fft_tma.cuh), with the
+// compile-time specialised complex64 rows of 2^13 and 2^14 elements
+// (fft_tma_ct.cuh) where they apply.
 #include "fft_kernels.cuh"
 #include "fft_tma.cuh"
+#include "fft_tma_ct.cuh"
 
 namespace pfft {
 
@@ -13,7 +16,20 @@ static int launch_tma_t(const PassArgs& a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+template <int LOGL>
+static int launch_tma_ct(const PassArgs& a, cudaStream_t s) {
+  static const int ok = configure_kernel(reinterpret_cast<const void*>(row_tma_ct_kernel<float2, LOGL>));
+  if (ok != 0) return -1;
+  dim3 grid(a.groups, a.batch), block((1 << LOGL) / 32);
+  row_tma_ct_kernel<float2, LOGL><<<grid, block, a.smem_bytes, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_tma(const PassArgs& a, int dtype, cudaStream_t s) {
+  if (dtype == 0 && a.T == 1 && a.nthreads == a.L / 32) {
+    if (a.L == 1 << 14) return launch_tma_ct<14>(a, s);
+    if (a.L == 1 << 13) return launch_tma_ct<13>(a, s);
+  }
   return dtype == 0 ? launch_tma_t<float2, 32>(a, s) : launch_tma_t<double2, 16>(a, s);
 }
 
