@@ -10,11 +10,15 @@
 // the index arithmetic:
 //
 //   * row i of column c of the tile sits at phys(i) + c with
-//     phys(i) = i T + floor(i / G), G = 32 / T rows per padded line (the
-//     padding of fphys: one element per 32).  Every row set a thread touches
-//     is b + r D with (b mod G) + (r D mod G) < G, so that
+//     phys(i) = (i + floor(i / 32)) T: one padding row after every 32 rows
+//     (for T = 1 the padding of fphys).  Both the Stockham exchanges and the
+//     sheared walk of a warp then hit every bank pair at most about twice,
+//     where the element-wise padding of fphys left the walk up to four-way
+//     conflicted for some shears.  Every row set a thread touches in the
+//     stages is b + r D with (b mod 32) + (r D mod 32) < 32, so that
 //     phys(b + r D) = phys(b) + phys(r D): a per-thread base and a constant
-//     offset per unrolled r, with no per-element integer work;
+//     offset per unrolled r, with no per-element integer work (the walk too
+//     when P >= 32);
 //   * the box points of the walk advance by one box addition per element,
 //     z_{j+1} = reduce(z_j + c_P) with c_P the box point of P g (g the
 //     generator of the column cycle), instead of a table load and a sum per
@@ -29,7 +33,7 @@ namespace pfft {
 
 template <int LOGT>
 __host__ __device__ __forceinline__ constexpr int ct_phys(int i) {
-  return (i << LOGT) + (i >> (5 - LOGT));
+  return (i + (i >> 5)) << LOGT;
 }
 
 // y <- reduce(y + c) for box points y, c of the box B (the reduction of
@@ -126,9 +130,8 @@ template <typename C, int DIM, int LOGL, int LOGT>
 __global__ void __launch_bounds__(ct_threads<LOGL, LOGT>(), 512 / ct_threads<LOGL, LOGT>())
     col_fast_ct_kernel(PassArgs a) {
   constexpr int R = 32;
-  constexpr int L = 1 << LOGL, T = 1 << LOGT, P = L / R, G = 32 >> LOGT;
+  constexpr int L = 1 << LOGL, T = 1 << LOGT, P = L / R;
   constexpr int TS = DIM <= 2 ? 2 : 4;
-  static_assert(P >= G, "walk offsets need P to be a multiple of G");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   C* stw = stage_table(sm, a);
@@ -153,7 +156,16 @@ __global__ void __launch_bounds__(ct_threads<LOGL, LOGT>(), 512 / ct_threads<LOG
     for (int r = 0; r < 4; ++r) z[r] = ct[r];
     box_add_t<DIM>(a.boxG, z, et);
   }
+  // shared-memory position of walk row i0 + j P (mod L), column tcol
   constexpr int WRAP = ct_phys<LOGT>(L);
+  auto walk_addr = [&](int j) {
+    if constexpr (P >= 32) {
+      return ct_phys<LOGT>(i0) + ct_phys<LOGT>(j * P) - (i0 + j * P >= L ? WRAP : 0);
+    } else {
+      const int i = i0 + j * P;
+      return ct_phys<LOGT>(i >= L ? i - L : i);
+    }
+  };
   C v[R];
   if (!walk_in) {
     const C* src = in + p0 + tcol + p * a.nD;
@@ -167,12 +179,11 @@ __global__ void __launch_bounds__(ct_threads<LOGL, LOGT>(), 512 / ct_threads<LOG
     cp_async_wait_all();
     __syncthreads();
   } else {
-    C* wb = smc + ct_phys<LOGT>(i0);
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       C x = __ldg(in + box_slot_t<DIM>(a.boxG, z));
       if (a.conj_in) x = cconj(x);
-      wb[ct_phys<LOGT>(j * P) - (i0 + j * P >= L ? WRAP : 0)] = x;
+      smc[walk_addr(j)] = x;
       if (j + 1 < R) box_add_t<DIM>(a.boxG, z, cP);
     }
     cp_async_wait_all();
@@ -196,10 +207,9 @@ __global__ void __launch_bounds__(ct_threads<LOGL, LOGT>(), 512 / ct_threads<LOG
 #pragma unroll
     for (int k = 0; k < R; ++k) wb[ct_phys<LOGT>(k * P)] = v[k];
     __syncthreads();
-    const C* rb = smc + ct_phys<LOGT>(i0);
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-      const C x = rb[ct_phys<LOGT>(j * P) - (i0 + j * P >= L ? WRAP : 0)];
+      const C x = smc[walk_addr(j)];
       out[box_slot_t<DIM>(a.boxG, z)] = cmake<C>(x.x * sx, x.y * sy);
       if (j + 1 < R) box_add_t<DIM>(a.boxG, z, cP);
     }
