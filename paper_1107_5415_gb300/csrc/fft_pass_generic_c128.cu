@@ -1,0 +1,6 @@
+// Odd-prime-radix transform passes, complex128 (16 points per thread).
+#include "fft_kernels.cuh"
+
+namespace pfft {
+int launch_generic_c128(const PassArgs& a, cudaStream_t s) { return launch_typed<double2, 16, false>(a, s); }
+}  // namespace pfft
