@@ -23,3 +23,21 @@ def test_reference_arm_json_line():
     assert j["config"]["workload"]
     assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["cores"] >= 1
     assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["e2e"]["value"] == j["value"]
+
+
+def test_smith_fftn_context_baseline_matches_oracle():
+    """The bench's library CPU transform (numpy fftn after the Smith gather)
+    agrees with the oracle's direct sum."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    import seeded_inputs as SI
+    from oracle import lattice as L
+
+    for M in (SI.M_SMALL_2D, [[8, 2], [2, -4]], [[3, 1, 2], [0, 2, 1], [1, 0, 4]], [[4, 1, 0], [0, 4, 1], [0, 0, 4]],
+              [[1, 0], [0, 1]]):
+        m = abs(L.det(M))
+        c = SI.complex_normal(1, m, 3, dtype=np.complex128)
+        assert np.allclose(bench.smith_fftn(M, c[0]), oracle.pattern_fft(M, c)[0], atol=1e-12)
