@@ -116,3 +116,34 @@ def test_row_permutation_walk(logl):
                 walk = hp + ((bp + k * cstep) & ((1 << ls) - 1))
                 assert (walk == direct).all(), (lg, inv, pad)
                 assert (bp + k * cstep).max() < 2 ** 31
+
+
+def _wavefronts(elems):
+    """Shared-memory wavefronts of one warp's 64-bit accesses: per bank, the
+    number of distinct 8-byte elements touching it; the maximum over banks."""
+    banks = {}
+    for e in set(int(x) for x in elems):
+        for b in (2 * e % 32, (2 * e + 1) % 32):
+            banks.setdefault(b, set()).add(e)
+    return max(len(v) for v in banks.values())
+
+
+@pytest.mark.parametrize("logl,logt", [(10, 3), (11, 2), (12, 1), (9, 4), (8, 4)])
+def test_column_tile_bank_spread(logl, logt):
+    """With one padding row per 32 rows, a warp's stage reads and the epilogue
+    writes take the minimum two wavefronts, and its sheared-walk reads at most
+    three for every shear tried (the element-wise padding needed up to eight)."""
+    L, T = 1 << logl, 1 << logt
+    P = L // R
+    nthr = P * T
+    worst_walk = 0
+    for alpha in (0, 1, 2, 3, 4, 5, 7, 12, 37, 100, L // 2 + 1, L - 1):
+        for w in range(0, nthr // 32, max(1, nthr // 32 // 4)):
+            th = np.arange(32) + 32 * w
+            tc, p = th & (T - 1), th >> logt
+            for r in range(0, R, 7):
+                if alpha == 0:
+                    assert _wavefronts(phys(p + P * r, logt) + tc) == 2
+                i = (p + (tc * alpha) % L + r * P) % L
+                worst_walk = max(worst_walk, _wavefronts(phys(i, logt) + tc))
+    assert worst_walk <= 3
