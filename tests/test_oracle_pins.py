@@ -506,3 +506,71 @@ def test_general_split_reduces_to_dirichlet_level(M, J):
     parts = oracle.split_general(M, J, np.stack([A, B]), c)
     d1, d2 = oracle.wavelet_level(M, J, oracle.DIRICHLET, c_hat=c)
     assert np.allclose(parts[0], d1, atol=1e-12) and np.allclose(parts[1], d2, atol=1e-12)
+
+
+# ------------------------------------------------- wavelet shift z (Section 6.2)
+def _wavelet_shift_golden():
+    rows = []
+    with open(os.path.join(GOLD, "wavelet_shift.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            t = line.split()
+            J = [[int(t[1]), int(t[2])], [int(t[3]), int(t[4])]]
+            z = [Fraction(t[5]), Fraction(t[6])]
+            u = [int(t[7]), int(t[8])]
+            rows.append((t[0], J, z, u))
+    return rows
+
+
+SHIFT_ROWS = _wavelet_shift_golden()
+
+
+@pytest.mark.parametrize("name,J,z,u", SHIFT_ROWS, ids=[r[0] for r in SHIFT_ROWS])
+def test_wavelet_shift_is_the_centred_pattern_point(name, J, z, u):
+    """The oracle's z is the non-zero point of Lambda(J) cap [-1/2, 1/2)^d
+    (Section 6.2), and u = J z."""
+    # the golden z is a non-zero pattern point of J in the half-open centred cube
+    Jz = [sum(J[i][k] * z[k] for k in range(2)) for i in range(2)]
+    assert all(x.denominator == 1 for x in Jz) and [int(x) for x in Jz] == u
+    assert any(x != 0 for x in z) and all(Fraction(-1, 2) <= x < Fraction(1, 2) for x in z)
+    assert oracle.wavelet_shift(J) == u
+
+
+WAVELET_DELTA_CASES = [([[8, 8], [-8, 8]], "J_diag_a"), ([[8, 0], [0, 8]], "J_diag_b"),
+                       ([[8, 0], [0, 8]], "J_x"), ([[8, 0], [0, 8]], "J_y"),
+                       ([[6, 2], [-2, 6]], "J_diag_a")]
+
+
+@pytest.mark.parametrize("M,name", WAVELET_DELTA_CASES)
+def test_wavelet_part_of_a_delta_matches_the_symbol_definition(M, name):
+    """For the input c_hat = e_h (one class h of G(M^T)) step 4 leaves
+    d2[g] = 2^{-1/2} conj(B(h)), g the class of h in G(N^T), with the wavelet
+    symbol of Section 6.2, B(h) = A(h + N^T l) exp(-2 pi i h^T N^{-1} z),
+    l the non-zero class of G(J^T).  The phase is evaluated here from the
+    golden z with exact rationals (N^{-1} by Gauss-Jordan elimination); the
+    oracle reaches it through u = J z and adj(M)."""
+    J, z = next((r[1], r[2]) for r in SHIFT_ROWS if r[0] == name)
+    m = abs(L.det(M))
+    N = oracle.exact_N(M, J)
+    Ninv = _gauss_jordan_inverse(N)
+    HM, HN = L.hnf(L.transpose(M)), L.hnf(L.transpose(N))
+    # a vector outside J^T Z^d: the non-zero class of G(J^T), found by brute force
+    JTinv = _gauss_jordan_inverse(L.transpose(J))
+    lvec = next(v for v in ([1, 0], [0, 1]) if any(
+        x.denominator != 1 for x in [sum(JTinv[i][k] * v[k] for k in range(2)) for i in range(2)]))
+    NTl = [sum(N[k][i] * lvec[k] for k in range(2)) for i in range(2)]
+    hs = [list(h) for h in L.box_points(HM)]
+    c = np.eye(m, dtype=np.complex128)  # row s: the delta at slot s
+    d1, d2 = oracle.wavelet_level(M, J, oracle.DIRICHLET, c_hat=c)
+    shifted = np.array([L.box_reduce(HM, [a + b for a, b in zip(h, NTl)]) for h in hs])
+    A_shift = oracle.scaling_symbol(M, J, shifted, oracle.DIRICHLET)
+    for s, h in enumerate(hs):
+        Nz = [sum(Ninv[i][k] * z[k] for k in range(2)) for i in range(2)]
+        t = sum(Fraction(h[i]) * Nz[i] for i in range(2))  # h^T N^{-1} z
+        t -= math.floor(t)
+        B = A_shift[s] * cmath.exp(-2j * math.pi * float(t))
+        g = L.slot_of(HN, L.box_reduce(HN, h))
+        assert abs(d2[s, g] - np.conj(B) / math.sqrt(2)) < 1e-13, (h, d2[s, g], B)
+        others = np.delete(d2[s], g)
+        assert np.abs(others).max(initial=0.0) == 0.0
