@@ -272,6 +272,66 @@ def bench_wavelet(pf, torch, peaks_hbm, steps=20, warmup=3):
                 out[name]["level1_kernel"] = {"avg_ms": ms, "achieved_gbs": gbs, "frac": gbs / peaks_hbm,
                                               "alg_bytes_per_launch": 16 * pts}
             plan.close()
+    out["step5"] = bench_step5(pf, torch, steps=steps, warmup=warmup)
+    return out
+
+
+def _next_pattern(M, J):
+    """N = J^{-1} M for |det J| = 2 (exact: adj(J) M / det J)."""
+    M = np.asarray(M, dtype=np.int64)
+    J = np.asarray(J, dtype=np.int64)
+    det = int(round(np.linalg.det(J)))
+    adj = np.array([[J[1, 1], -J[0, 1]], [-J[1, 0], J[0, 0]]], dtype=np.int64)
+    P = adj @ M
+    assert (P % det == 0).all()
+    return (P // det).tolist()
+
+
+def bench_step5(pf, torch, steps=20, warmup=3):
+    """Section 5.3 step 5 on the 12-level workload (Dirichlet symbol): the
+    split cascade alone, and the cascade followed by the inverse pattern FFT
+    of each of its 13 parts on G(N_l^T) (12 wavelet parts, one scaling part),
+    with the step-5 transforms in the plain fp32 form and in the
+    split-precision tensor-core form.  Input points of the cascade per second;
+    the tensor-core result is compared with the fp32 one over all parts (each
+    form's error against the FP64 oracle is checked by the tests)."""
+    w = SI.WORKLOADS[WAVELET]
+    M, batch, levels = w["M"], w["batch"], w["levels"]
+    Js = SI.wavelet_dilations(levels)
+    split = pf.WaveletSplit(M, Js, pf.PWT_DIRICHLET, 0.125, batch)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w["seed"])
+    c = torch.randn(batch, split.sizes[0], dtype=torch.complex64, device="cuda", generator=gen)
+    sc, wv = split.decompose(c)
+    Ns, cur = [], M
+    for J in Js:
+        cur = _next_pattern(cur, J)
+        Ns.append(cur)
+    parts = list(zip(Ns, wv)) + [(Ns[-1], sc)]
+    pts = split.sizes[0] * batch
+    out = {"workload": "12-level cascade (Dirichlet) + inverse pattern FFT of every part (Section 5.3 step 5)"}
+    ms_split = _time_ms(torch, lambda: split.decompose(c), steps, warmup)
+    out["split_only"] = {"ms": ms_split, "value": pts / (ms_split * 1e-3), "unit": "points/s"}
+    results = {}
+    for form in ("fp32", "tc_split"):
+        plans = [pf.PatternFFT(N, batch, tc_split=(form == "tc_split")) for N, _ in parts]
+        outs = [torch.empty_like(x) for _, x in parts]
+
+        def chain():
+            s_, w_ = split.decompose(c)
+            for p_, x_, o_ in zip(plans, w_ + [s_], outs):
+                p_.inverse(x_, o_)
+
+        ms = _time_ms(torch, chain, steps, warmup)
+        results[form] = torch.cat([o.flatten() for o in outs])
+        out[form] = {"ms": ms, "value": pts / (ms * 1e-3), "unit": "points/s",
+                     "step5_ms": ms - ms_split}
+        for p_ in plans:
+            p_.close()
+    num = torch.linalg.vector_norm(results["tc_split"] - results["fp32"]).item()
+    out["tc_split"]["rel_l2_vs_fp32"] = num / torch.linalg.vector_norm(results["fp32"]).item()
+    out["tc_split"]["speedup_vs_fp32"] = out["fp32"]["ms"] / out["tc_split"]["ms"]
+    split.close()
     return out
 
 

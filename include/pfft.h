@@ -83,9 +83,11 @@ enum {
   /* Split-precision tensor-core form (PFFT_C64 only): the radix-16 and
    * radix-32 stages run as dense DFT-matrix products on the tensor cores in
    * fp16 with fp32 accumulation, each operand split into hi + lo fp16 halves
-   * (three products per tile), which recovers fp32-level accuracy.  Values
-   * entering those stages must stay below the fp16 range (|x| < 65504).
-   * Without the flag every stage runs in plain fp32 on the CUDA cores. */
+   * (three products per tile), which recovers fp32-level accuracy.  Each
+   * butterfly is scaled by a power of two before the split and back after
+   * the product (exact), so the accuracy holds for data of any magnitude
+   * within the fp32 range.  Without the flag every stage runs in plain fp32
+   * on the CUDA cores. */
   PFFT_FLAG_TC_SPLIT = 1u,
   /* Smith-coordinate layout (the reordering-free order of Section 4): the
    * input is indexed by lambda = (lambda_1 .. lambda_d), lambda_j in
@@ -175,6 +177,18 @@ pfft_status pfft_plan_destroy(pfft_plan p);
  * kernels set (PFFT_ERR_TIMEOUT when a bounded wait on an asynchronous copy
  * gave up; PFFT_OK otherwise) and clears it. */
 pfft_status pfft_last_device_status(pfft_plan p, void* stream);
+
+/* Iteration limit of the first bounded wait of the bulk-copy row pass (the
+ * wait for a row's asynchronous copies to land in shared memory).
+ * spins >= 0 sets it (values above 2^32 - 1 are clamped), spins < 0
+ * restores the default of 2^22 iterations.  With 0 the wait gives up at
+ * once, which exercises the timeout path: the kernel records
+ * PFFT_ERR_TIMEOUT in the plan's status word (pfft_last_device_status),
+ * waits with the default limit for its own copies, and returns without
+ * transforming, so the output of such a call is undefined.  Host-side
+ * setting, applies to later calls.  Returns PFFT_ERR_UNSUPPORTED for a plan
+ * whose row pass does not stage through bulk copies (no such wait). */
+pfft_status pfft_set_wait_limit(pfft_plan p, int64_t spins);
 
 /* Per-kernel timing of a plan's launches (CUDA events recorded on the
  * launching stream around each kernel).  enable != 0 starts recording and

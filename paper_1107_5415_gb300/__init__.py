@@ -29,7 +29,7 @@ from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_BATCH_RADIX8,
                     pfft_batch_schedule, pfft_device_index_map, pwt_merge_general, pwt_split_general,
                     pfft_forward, pfft_hermite_normal_form, pfft_index_map, pfft_inverse, pfft_plan_create,
                     pfft_last_device_status, pfft_plan_destroy, pfft_plan_info, pfft_profile_enable, pfft_profile_read,
-                    pfft_smith_normal_form, pwt_adjoint, pwt_decompose, pwt_plan_create, pwt_plan_destroy,
+                    pfft_set_wait_limit, pfft_smith_normal_form, pwt_adjoint, pwt_decompose, pwt_plan_create, pwt_plan_destroy,
                     pwt_plan_info, pwt_reconstruct)
 
 __all__ = [
@@ -40,7 +40,7 @@ __all__ = [
     "PfftError", "PFFT_C64", "PFFT_C128", "PWT_DIRICHLET", "PWT_DLVP",
     "PFFT_MAP_INPUT_BOX", "PFFT_MAP_OUTPUT_BOX", "PFFT_MAP_INPUT_SNF", "PFFT_MAP_OUTPUT_SNF",
     "pfft_plan_create", "pfft_plan_info", "pfft_index_map", "pfft_device_index_map", "pfft_forward",
-    "pfft_inverse", "pfft_plan_destroy", "pfft_last_device_status", "pfft_profile_enable", "pfft_profile_read",
+    "pfft_inverse", "pfft_plan_destroy", "pfft_last_device_status", "pfft_set_wait_limit", "pfft_profile_enable", "pfft_profile_read",
     "pfft_hermite_normal_form", "pfft_smith_normal_form", "pwt_plan_create", "pwt_plan_info",
     "pwt_decompose", "pwt_reconstruct", "pwt_adjoint", "pwt_plan_destroy", "library_path",
 ]

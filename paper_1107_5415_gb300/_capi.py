@@ -59,6 +59,7 @@ _SIGS = {
     "pfft_inverse": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "pfft_plan_destroy": (ctypes.c_int, [_vp]),
     "pfft_last_device_status": (ctypes.c_int, [_vp, _vp]),
+    "pfft_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "pfft_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pfft_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_char_p), _i64p,
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int,
@@ -186,6 +187,11 @@ def pfft_last_device_status(plan, stream: int):
     _check(lib().pfft_last_device_status(plan, stream), "pfft_last_device_status")
 
 
+def pfft_set_wait_limit(plan, spins: int):
+    """Iteration limit of the row pass's first bounded wait (< 0: default)."""
+    _check(lib().pfft_set_wait_limit(plan, int(spins)), "pfft_set_wait_limit")
+
+
 def pfft_plan_destroy(plan):
     _check(lib().pfft_plan_destroy(plan), "pfft_plan_destroy")
 
@@ -256,6 +262,8 @@ def pwt_decompose_noalloc(M, Js, symbol: int, eta: float, batch: int, c_hat_ptr:
     levels = Ja.shape[0]
     if Ja.shape != (levels, d, d):
         raise ValueError("J must have shape [levels, d, d]")
+    if len(wavelet_ptrs) != levels:
+        raise ValueError("need one wavelet pointer per level")
     ja, jp = _i64(Ja.reshape(-1))
     arr = _ptr_array(wavelet_ptrs)
     _check(lib().pwt_decompose_noalloc(d, p, levels, jp, int(symbol), float(eta), int(batch), c_hat_ptr,

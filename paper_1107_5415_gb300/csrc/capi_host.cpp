@@ -30,7 +30,11 @@ static pfft_status load(int d, const int64_t* M, IMat& A) {
     if (M[i] >= (int64_t(1) << 24) || M[i] <= -(int64_t(1) << 24)) return PFFT_ERR_OVERFLOW;
     A.a[i] = M[i];
   }
-  if (determinant(A) == 0) return PFFT_ERR_SINGULAR;
+  try {
+    if (determinant(A) == 0) return PFFT_ERR_SINGULAR;
+  } catch (const LatticeError& e) {
+    return pfft_status(e.code);
+  }
   return PFFT_OK;
 }
 

@@ -631,6 +631,7 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
     p->tw_n = colt ? col_n : nD;
     p->ts = ts;
     p->status = P.status;
+    p->spin_limit = kSpinLimit;
     set_box(p->boxH, P.H);
     set_box(p->boxG, P.G);
     p->pi_arith = arith.pi_arith;
@@ -940,6 +941,13 @@ extern "C" pfft_status pfft_profile_read(pfft_plan p, const char** names, int64_
                                          int cap, int* n) {
   if (!p) return PFFT_ERR_ARG;
   return p->prof.read(names, launches, ms, cap, n) ? PFFT_OK : PFFT_ERR_CUDA;
+}
+
+extern "C" pfft_status pfft_set_wait_limit(pfft_plan p, int64_t spins) {
+  if (!p) return PFFT_ERR_ARG;
+  if (!p->rowp.tma) return PFFT_ERR_UNSUPPORTED;
+  p->rowp.spin_limit = spins < 0 ? kSpinLimit : uint32_t(std::min<int64_t>(spins, int64_t(UINT32_MAX)));
+  return PFFT_OK;
 }
 
 extern "C" pfft_status pfft_last_device_status(pfft_plan p, void* stream) {

@@ -29,6 +29,9 @@ namespace pfft {
 enum MapMode { MAP_WS = 0, MAP_BOX_H = 1, MAP_BOX_G = 2 };
 
 constexpr int kMaxStages = 16;
+// Default iteration limit of the bounded mbarrier waits of the bulk-copy
+// row passes (far above the time a row's copies take to land).
+constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kMaxSub = 3;
 constexpr int kMaxThreads = 512;
 constexpr int kRadixOrder[7] = {16, 8, 4, 2, 3, 5, 7};
@@ -109,6 +112,7 @@ struct alignas(16) PassArgs {
   int nruns;
   int bar_smem_off;   // byte offset of the mbarrier in shared memory
   int* status;        // device status word (PFFT_ERR_TIMEOUT on a timed-out wait)
+  uint32_t spin_limit;  // iterations of the first mbarrier wait before it gives up
   // workspace-order staging of the TMA row pass in 2^pi_lg blocks of 2^pi_lspan
   // positions, each followed by stg_pad elements (0: one dense block), so that
   // the permuted accesses of lanes with equal mu >> pi_lg hit different banks

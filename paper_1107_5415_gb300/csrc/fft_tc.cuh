@@ -9,8 +9,12 @@
 // a = a_hi + a_lo with a_hi = fp16(a) and a_lo = fp16(a - a_hi), and the
 // product is accumulated in fp32 as a_hi b_hi + a_hi b_lo + a_lo b_hi, which
 // keeps about 22 significant bits (the dropped a_lo b_lo term is below the
-// fp32 rounding of the sums).  Inputs must stay below the fp16 range
-// (|x| < 65504) at every stage.
+// fp32 rounding of the sums).  Each butterfly is scaled by a power of two
+// before the split so that its largest input lies in [2^10, 2^11) (the four
+// lanes holding its inputs agree on the factor through two shuffles), and its
+// outputs are scaled back after the accumulation: both steps are exact in
+// fp32, so the fp16 halves neither overflow nor fall into the subnormal range
+// for data of any magnitude from 2^-116 up to the fp32 range.
 //
 // The A operand (the DFT matrix) is the same for every butterfly: each CTA
 // writes its fragments, hi and lo, to shared memory once, in the register
@@ -118,8 +122,10 @@ __device__ __noinline__ void run_tc_stage(float2* sm, const PassArgs& a, const S
     ebase = COLS ? base * a.T + tt : tt * a.L + base;
   };
   float acc[G][MT][4];
+  int ex_of[G];
 #pragma unroll
   for (int u = 0; u < G; ++u) {
+    ex_of[u] = 0;
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
@@ -143,6 +149,21 @@ __device__ __noinline__ void run_tc_stage(float2* sm, const PassArgs& a, const S
     } else {
 #pragma unroll
       for (int q = 0; q < NR; ++q) xr[q] = xi[q] = 0.f;
+    }
+    // power-of-two scale of this butterfly (lanes 4 g .. 4 g + 3 hold its inputs)
+    float mx = 0.f;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) mx = fmaxf(mx, fmaxf(fabsf(xr[q]), fabsf(xi[q])));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    int ex = mx > 0.f ? 10 - ilogbf(mx) : 0;
+    ex = ex > 126 ? 126 : (ex < -126 ? -126 : ex);  // 2^ex and 2^-ex both normal
+    ex_of[u] = ex;
+    const float up = __int_as_float((127 + ex) << 23);
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      xr[q] *= up;
+      xi[q] *= up;
     }
     uint32_t bh[KT][2], bl[KT][2];
 #pragma unroll
@@ -172,6 +193,9 @@ __device__ __noinline__ void run_tc_stage(float2* sm, const PassArgs& a, const S
 #pragma unroll
     for (int c = 0; c < 2; ++c) {  // D columns 2t, 2t + 1
       const int bf = grp * 8 + 2 * t + c;
+      // undo the scale of butterfly 2t + c (held by lane 4 (2t + c))
+      const int ex = __shfl_sync(0xffffffffu, ex_of[u], (2 * t + c) * 4);
+      const float down = __int_as_float((127 - ex) << 23);
       if (bf >= nbf) continue;
       int ebase, k, j;
       locate(bf, ebase, k, j);
@@ -181,7 +205,8 @@ __device__ __noinline__ void run_tc_stage(float2* sm, const PassArgs& a, const S
 #pragma unroll
         for (int h = 0; h < 2; ++h) {  // D rows g, g + 8
           const int so = 16 * mt + g + 8 * h;
-          sm[phys<PAD>(ob + so * ostep)] = make_float2(acc[u][mt][2 * h + c], acc[u][mt + HALF][2 * h + c]);
+          sm[phys<PAD>(ob + so * ostep)] =
+              make_float2(acc[u][mt][2 * h + c] * down, acc[u][mt + HALF][2 * h + c] * down);
         }
     }
   }

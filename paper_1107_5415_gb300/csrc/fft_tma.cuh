@@ -21,7 +21,6 @@
 
 namespace pfft {
 
-constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kStatusTimeout = 8;  // PFFT_ERR_TIMEOUT
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -43,8 +42,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint32_t limit = kSpinLimit) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_tma_kernel(PassArgs a) {
     bulk_g2s(sm + c * (span + a.stg_pad), in + (size_t)row * a.nD + c * span, uint32_t(span) * uint32_t(sizeof(C)),
              bar);
   }
-  if (!mbar_wait_bounded(bar, 0)) {
+  if (!mbar_wait_bounded(bar, 0, a.spin_limit)) {
     if (threadIdx.x == 0) atomicExch(a.status, kStatusTimeout);
     mbar_wait_bounded(bar, 0);  // let this CTA's own copies land before leaving
     cp_async_wait_all();

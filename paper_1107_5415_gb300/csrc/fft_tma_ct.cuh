@@ -68,7 +68,7 @@ __global__ void __launch_bounds__((1 << LOGL) / 32, (1 << 14) >> LOGL) row_tma_c
     const int pos = col_pos(a, p + P * k);
     return a.stg_pad ? pos + (pos >> a.pi_lspan) * a.stg_pad : pos;
   };
-  if (!mbar_wait_bounded(bar, 0)) {
+  if (!mbar_wait_bounded(bar, 0, a.spin_limit)) {
     if (threadIdx.x == 0) atomicExch(a.status, kStatusTimeout);
     mbar_wait_bounded(bar, 0);  // let this CTA's own copies land before leaving
     cp_async_wait_all();

@@ -72,9 +72,42 @@ i64 modinv(i64 a, i64 m) {  // extended Euclid
   return posmod(x0, m);
 }
 
+// Checked i128 steps: an intermediate that leaves the i128 range is an
+// overflow error, never a wrapped value.
+static i128 mul_checked(i128 a, i128 b) {
+  i128 r;
+  if (__builtin_mul_overflow(a, b, &r)) throw LatticeError{PFFT_ERR_OVERFLOW, "determinant overflow"};
+  return r;
+}
+static i128 add_checked(i128 a, i128 b) {
+  i128 r;
+  if (__builtin_add_overflow(a, b, &r)) throw LatticeError{PFFT_ERR_OVERFLOW, "determinant overflow"};
+  return r;
+}
+
+// Cofactor expansion along the first row.  For d <= 4 and entries below 2^24
+// every term is a product of d entries (< 2^96), so the sum is exact; larger
+// inputs raise PFFT_ERR_OVERFLOW through the checked steps.
+static i128 det_cofactor(const std::vector<i128>& A, int d) {
+  if (d == 1) return A[0];
+  std::vector<i128> minor(size_t(d - 1) * (d - 1));
+  i128 s = 0;
+  for (int j = 0; j < d; ++j) {
+    if (A[j] == 0) continue;
+    for (int r = 1; r < d; ++r)
+      for (int c = 0, cc = 0; c < d; ++c)
+        if (c != j) minor[size_t(r - 1) * (d - 1) + cc++] = A[size_t(r) * d + c];
+    const i128 t = mul_checked(A[j], det_cofactor(minor, d - 1));
+    s = add_checked(s, (j & 1) ? -t : t);
+  }
+  return s;
+}
+
 i64 determinant(const IMat& M) {
   const int d = M.d;
   std::vector<i128> A(M.a.begin(), M.a.end());
+  if (d <= 4) return narrow(det_cofactor(A, d));
+  // fraction-free elimination (Bareiss) for larger d, every product checked
   auto at = [&](int i, int j) -> i128& { return A[size_t(i) * d + j]; };
   i128 prev = 1;
   int sign = 1;
@@ -89,7 +122,7 @@ i64 determinant(const IMat& M) {
     }
     for (int i = k + 1; i < d; ++i)
       for (int j = k + 1; j < d; ++j) {
-        i128 v = at(i, j) * at(k, k) - at(i, k) * at(k, j);
+        const i128 v = add_checked(mul_checked(at(i, j), at(k, k)), -mul_checked(at(i, k), at(k, j)));
         at(i, j) = v / prev;  // exact division (Bareiss)
         if (at(i, j) > kLimit || at(i, j) < -kLimit)
           throw LatticeError{PFFT_ERR_OVERFLOW, "determinant overflow"};

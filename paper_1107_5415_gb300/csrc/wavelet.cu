@@ -591,6 +591,7 @@ extern "C" pfft_status pwt_decompose_noalloc(int d, const int64_t* M, int levels
     st = pfft_status(e.code);
   }
   if (st != PFFT_OK) return st;
+  if (P.sizes[0] * batch >= (int64_t(1) << 40)) return PFFT_ERR_OVERFLOW;  // as pwt_plan_create
   // two ping-pong halves of the scratch hold the scaling parts of levels < L
   const size_t half = kNoAllocScratchElems / 2;
   if (levels > 1 && size_t(P.sizes[0] / 2) * size_t(batch) > half) return PFFT_ERR_OVERFLOW;

@@ -89,6 +89,43 @@ def test_host_errors():
     assert e.value.status == 1  # PFFT_ERR_ARG
 
 
+def test_noalloc_binding_needs_one_wavelet_pointer_per_level():
+    """The C side reads wavelets[l] for every level: a short list is refused
+    before the call."""
+    with pytest.raises(ValueError):
+        _capi.pwt_decompose_noalloc(SI.M_WAVELET_2D, SI.wavelet_dilations(3), pf.PWT_DIRICHLET, 0.125, 1,
+                                    1, 2, [3, 4], 0)
+
+
+def test_dense_large_entries_overflow_cleanly():
+    """A dense 4 x 4 matrix with entries near the 2^24 cap has |det| near 2^94
+    and 3 x 3 minors near 2^70: the planner's exact determinant must report
+    PFFT_ERR_OVERFLOW, not a wrapped i128 value."""
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        M = rng.integers(-(1 << 24) + 1, 1 << 24, size=(4, 4))
+        assert abs(L.det(M.tolist())) >= 1 << 63
+        with pytest.raises(pf.PfftError) as e:
+            pf.pfft_hermite_normal_form(M)
+        assert e.value.status == 3  # PFFT_ERR_OVERFLOW
+
+
+def test_large_entries_small_determinant_exact():
+    """Entries near 2^22 whose products cancel down to |det M| = 3: the
+    determinant and the Hermite form stay exact (oracle's Python integers)."""
+    rng = np.random.default_rng(7)
+    done = 0
+    while done < 5:
+        A = [[1 if i == j else (int(rng.integers(-2**11, 2**11)) if i > j else 0) for j in range(4)] for i in range(4)]
+        B = [[1 if i == j else (int(rng.integers(-2**11, 2**11)) if i < j else 0) for j in range(4)] for i in range(4)]
+        D = [[int(i == j) * (3 if i == 3 else 1) for j in range(4)] for i in range(4)]
+        M = L.matmul(L.matmul(B, D), A)
+        if max(abs(x) for r in M for x in r) >= 1 << 24:
+            continue
+        assert pf.pfft_hermite_normal_form(M).tolist() == L.hnf(M)
+        done += 1
+
+
 @pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU path")
 def test_plan_without_gpu_fails_loudly():
     with pytest.raises(pf.PfftError) as e:

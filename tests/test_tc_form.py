@@ -68,3 +68,20 @@ def test_tc_rejects_complex128():
     with pytest.raises(pf.PfftError) as e:
         pf.PatternFFT([[16, 0], [0, 16]], 1, torch.complex128, tc_split=True)
     assert e.value.status == 5
+
+
+@pytest.mark.parametrize("scale", [1e-3, 1e3, 1e-30, 1e30])
+@pytest.mark.parametrize("M", [[[32, 0], [0, 64]], [[4, 1], [0, 8192]]], ids=["32x64", "split32768"])
+def test_tc_accuracy_is_scale_free(M, scale):
+    """Inputs scaled far from unit size (small enough for fp16 subnormals, or
+    beyond the fp16 range) keep the complex64 bar against the oracle: each
+    butterfly is rescaled by a power of two around the split."""
+    m = abs(L.det(M))
+    plan = pf.PatternFFT(M, 1, tc_split=True)
+    c = SI.complex_normal(1, m, seed=5).astype(np.complex128) * scale
+    slots = SI.sample_slots(m, min(m, 2048))
+    ref = oracle.pattern_fft(M, c, out_slots=slots)
+    got = plan.forward(_gpu(c.astype(np.complex64))).cpu().numpy()
+    err = rel_l2(got[:, slots], ref)
+    print(f"tc {M} x {scale:g}: rel-L2 {err:.2e}")
+    assert err <= 1e-5
