@@ -732,6 +732,27 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
       P.rowp.nruns = maxr;
       P.rowp.bar_smem_off = (P.rowp.smem_bytes + 15) & ~15;
       P.rowp.smem_bytes = P.rowp.bar_smem_off + 16;
+      // rows of 2^14 complex64 elements: the persistent pipelined row pass,
+      // shared memory [S: the row + staging pads | X: exchange | stage table | mbarrier]
+      if (P.dtype == PFFT_C64 && P.rowp.L == (1 << kPipeLogL) && P.rowp.nthreads == 512 &&
+          P.rowp.fast_tail == 16 && P.rowp.fast_nmain == 2) {
+        const int nblk = P.rowp.stg_pad ? (1 << P.rowp.pi_lg) : 1;
+        const int s_el = P.rowp.L + nblk * P.rowp.stg_pad;
+        const int x_off = (s_el + 15) & ~15;
+        const int stw_off = (x_off + kPipeX + 15) & ~15;
+        const int bar_off = ((stw_off + P.rowp.stw_n) * 8 + 15) & ~15;
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P.device) != cudaSuccess || nsm < 1)
+          return PFFT_ERR_CUDA;
+        if (bar_off + 16 <= 227 * 1024) {
+          P.rowp.pipe = 1;
+          P.rowp.pipe_x_off = x_off;
+          P.rowp.pipe_grid = nsm;
+          P.rowp.stw_smem_off = stw_off;
+          P.rowp.bar_smem_off = bar_off;
+          P.rowp.smem_bytes = bar_off + 16;
+        }
+      }
     }
   }
   if (!idx.empty()) {

@@ -32,6 +32,12 @@ constexpr int kMaxStages = 16;
 // Default iteration limit of the bounded mbarrier waits of the bulk-copy
 // row passes (far above the time a row's copies take to land).
 constexpr uint32_t kSpinLimit = 1u << 22;
+// Persistent pipelined row pass (fft_row_pipe.cuh): row length 2^kPipeLogL,
+// exchanged and stored in two rounds of kPipeHalf elements through a buffer
+// of kPipeX elements (one padding element per 16).
+constexpr int kPipeLogL = 14;
+constexpr int kPipeHalf = 1 << (kPipeLogL - 1);
+constexpr int kPipeX = kPipeHalf + (kPipeHalf >> 4);
 constexpr int kMaxSub = 3;
 constexpr int kMaxThreads = 512;
 constexpr int kRadixOrder[7] = {16, 8, 4, 2, 3, 5, 7};
@@ -113,6 +119,10 @@ struct alignas(16) PassArgs {
   int bar_smem_off;   // byte offset of the mbarrier in shared memory
   int* status;        // device status word (PFFT_ERR_TIMEOUT on a timed-out wait)
   uint32_t spin_limit;  // iterations of the first mbarrier wait before it gives up
+  // persistent pipelined row pass (fft_row_pipe.cuh): rows of 2^14 complex64
+  int pipe;            // 1: use row_pipe_kernel
+  int pipe_x_off;      // element offset of its exchange buffer in shared memory
+  int pipe_grid;       // CTAs of its launch (one per SM)
   // workspace-order staging of the TMA row pass in 2^pi_lg blocks of 2^pi_lspan
   // positions, each followed by stg_pad elements (0: one dense block), so that
   // the permuted accesses of lanes with equal mu >> pi_lg hit different banks

@@ -4,6 +4,7 @@
 #include "fft_kernels.cuh"
 #include "fft_tma.cuh"
 #include "fft_tma_ct.cuh"
+#include "fft_row_pipe.cuh"
 
 namespace pfft {
 
@@ -25,7 +26,29 @@ static int launch_tma_ct(const PassArgs& a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+template <bool FWD>
+static int launch_pipe_t(const PassArgs& a, cudaStream_t s) {
+  static const int ok = configure_kernel(reinterpret_cast<const void*>(row_pipe_kernel<FWD>));
+  if (ok != 0) return -1;
+  const int total = a.LB * a.batch;
+  dim3 grid(total < a.pipe_grid ? total : a.pipe_grid), block(1 << (kPipeLogL - 5));
+  row_pipe_kernel<FWD><<<grid, block, a.smem_bytes, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// The pipelined row pass serves the two-pass directions: forward (box ->
+// workspace, no conjugation, unit scale) and inverse (workspace -> box,
+// conjugated output, scaled).
+static int launch_pipe(const PassArgs& a, cudaStream_t s) {
+  if (a.load_mode == MAP_BOX_H && a.store_mode == MAP_WS && !a.conj_in && !a.conj_out && a.scale == 1.0)
+    return launch_pipe_t<true>(a, s);
+  if (a.load_mode == MAP_WS && a.store_mode == MAP_BOX_H && !a.conj_in && a.conj_out)
+    return launch_pipe_t<false>(a, s);
+  return -1;
+}
+
 int launch_tma(const PassArgs& a, int dtype, cudaStream_t s) {
+  if (a.pipe && dtype == 0) return launch_pipe(a, s);
   if (dtype == 0 && a.T == 1 && a.nthreads == a.L / 32) {
     if (a.L == 1 << 14) return launch_tma_ct<14>(a, s);
     if (a.L == 1 << 13) return launch_tma_ct<13>(a, s);
