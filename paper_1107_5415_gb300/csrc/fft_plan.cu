@@ -745,6 +745,25 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P.device) != cudaSuccess || nsm < 1)
           return PFFT_ERR_CUDA;
         if (bar_off + 16 <= 227 * 1024) {
+          // outputs stored from registers: the workspace when the permutation
+          // multiplier is 1 and lanes form runs of >= 4 elements (32 B); the
+          // box when every row is made of runs of one power-of-two length >= 32
+          int direct = 0, lrun = 0;
+          if (P.rowp.pi_arith && P.rowp.pi_inv == 1 && P.rowp.pi_lg <= 3) direct |= 1;
+          for (int l = 5; l <= kPipeLogL && !(direct & 2); ++l) {
+            bool uni = maxr == (1 << (kPipeLogL - l));
+            for (int r = 0; r < LB && uni; ++r) {
+              uni = per[r].size() == size_t(maxr);
+              for (size_t j = 0; j < per[r].size() && uni; ++j)
+                uni = per[r][j][0] == int(j) << l && per[r][j][2] == 1 << l;
+            }
+            if (uni) {
+              direct |= 2;
+              lrun = l;
+            }
+          }
+          P.rowp.pipe_direct = direct;
+          P.rowp.pipe_lrun = lrun;
           P.rowp.pipe = 1;
           P.rowp.pipe_x_off = x_off;
           P.rowp.pipe_grid = nsm;

@@ -123,6 +123,8 @@ struct alignas(16) PassArgs {
   int pipe;            // 1: use row_pipe_kernel
   int pipe_x_off;      // element offset of its exchange buffer in shared memory
   int pipe_grid;       // CTAs of its launch (one per SM)
+  int pipe_direct;     // 1: output stored from registers (see fft_row_pipe.cuh)
+  int pipe_lrun;       // log2 of the uniform run length of the box rows (0: runs not uniform)
   // workspace-order staging of the TMA row pass in 2^pi_lg blocks of 2^pi_lspan
   // positions, each followed by stg_pad elements (0: one dense block), so that
   // the permuted accesses of lanes with equal mu >> pi_lg hit different banks

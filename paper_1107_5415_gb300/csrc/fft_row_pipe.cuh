@@ -66,7 +66,13 @@ __device__ __forceinline__ void pipe_x2_read(float2* v, const float2* X, int p) 
 
 // FWD: the forward row pass (box runs -> workspace row); else the inverse
 // (workspace row -> box runs, conjugated and scaled).
-template <bool FWD>
+// DIRECT: the output leaves from the registers with plain stores (workspace
+// rows whose permutation keeps lanes in runs, box rows made of uniform runs);
+// else it is staged through X in two rounds of bulk copies.
+// X1S: exchange 1 in one round through S and X together, the next row's
+// copies issued after it; else in two rounds through X, the copies issued
+// as soon as the row has been read from S.
+template <bool FWD, bool DIRECT, bool X1S>
 __global__ void __launch_bounds__(512, 1) row_pipe_kernel(PassArgs a) {
   using C = float2;
   constexpr int R = 32, L = 1 << kPipeLogL, P = L / R, LP = kPipeLogL - 5;
@@ -156,20 +162,34 @@ __global__ void __launch_bounds__(512, 1) row_pipe_kernel(PassArgs a) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[16 * q + r] = cmul(v[16 * q + r], fs_twiddle<C>(a, row, p + P * (q + 2 * r)));
     }
-    if (issuer()) bulk_wait_read_all();  // the previous row's output has left X
-    __syncthreads();                   // S is read: the next row may land in it
-    if (gn < total) issue_load(gn);
-
-    // ---- tail stage (radix 16) and exchange 1, one round per butterfly
+    if (!DIRECT && issuer()) bulk_wait_read_all();  // the previous row's output has left X
+    __syncthreads();  // S is read
+    if constexpr (X1S) {
+      // ---- tail stage (radix 16) and exchange 1 in one round through S and X
+      dft16(v);
+      dft16(v + 16);
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      dft16(v + 16 * q);
+      for (int q = 0; q < 2; ++q)
 #pragma unroll
-      for (int r = 0; r < 16; ++r) X[xphys((p << 4) | r)] = v[16 * q + r];
+        for (int r = 0; r < 16; ++r) S[xphys((q << 13) | (p << 4) | r)] = v[16 * q + r];
       __syncthreads();
 #pragma unroll
-      for (int r = 0; r < 16; ++r) v[16 * q + r] = X[xphys((r << 9) | p)];
-      __syncthreads();
+      for (int r = 0; r < 32; ++r) v[r] = S[xphys((r << 9) | p)];
+      __syncthreads();  // S is free: the next row may land in it
+      if (gn < total) issue_load(gn);
+    } else {
+      if (gn < total) issue_load(gn);
+      // ---- tail stage (radix 16) and exchange 1, one round per butterfly
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        dft16(v + 16 * q);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) X[xphys((p << 4) | r)] = v[16 * q + r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[16 * q + r] = X[xphys((r << 9) | p)];
+        __syncthreads();
+      }
     }
     // ---- stage 0 (Ns = 16) and exchange 2
     {
@@ -194,8 +214,33 @@ __global__ void __launch_bounds__(512, 1) row_pipe_kernel(PassArgs a) {
     if (p) main_twiddle<C, R>(v, stw + a.stw_off[1] + p * 5);
     dft_pow2<C, R>(v);
 
-    // ---- output in two rounds through X
-    if constexpr (FWD) {
+    // ---- output
+    if constexpr (FWD && DIRECT) {
+      // workspace position ((p mod 2^lg) << ls) + (p >> lg) + k 2^(9 - lg)
+      // (permutation multiplier 1): lanes write runs of 2^(5 - lg) elements
+      if (a.fs_na > 1) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = cmul(v[k], fs_twiddle<C>(a, row, p + P * k));
+      }
+      const int lg = a.pi_lg;
+      C* out = out_all + (int64_t)b * a.m + (size_t)row * a.nD + ((p & ((1 << lg) - 1)) << a.pi_lspan) + (p >> lg);
+      const int cst = P >> lg;
+#pragma unroll
+      for (int k = 0; k < R; ++k) out[k * cst] = v[k];
+    } else if constexpr (!FWD && DIRECT) {
+      // box rows of uniform runs of 2^lrun elements: element e lies in run e >> lrun
+      C* out = out_all + (int64_t)b * a.m;
+      const int4* runs = reinterpret_cast<const int4*>(a.runs) + (size_t)row * a.nruns;
+      const int lrun = a.pipe_lrun, mrun = (1 << lrun) - 1;
+      const float sx = float(a.scale), sy = -sx;  // conjugate and scale
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int e = p + P * r;
+        const C x = v[r];
+        out[__ldg(&runs[e >> lrun].y) + (e & mrun)] = cmake<C>(x.x * sx, x.y * sy);
+      }
+    } else if constexpr (FWD) {
+      // ---- output in two rounds through X
       if (a.fs_na > 1) {
 #pragma unroll
         for (int k = 0; k < R; ++k) v[k] = cmul(v[k], fs_twiddle<C>(a, row, p + P * k));
@@ -246,7 +291,7 @@ __global__ void __launch_bounds__(512, 1) row_pipe_kernel(PassArgs a) {
       }
     }
   }
-  bulk_wait_all();  // every output copy of this CTA is complete
+  if constexpr (!DIRECT) bulk_wait_all();  // every output copy of this CTA is complete
 }
 
 }  // namespace pfft

@@ -26,13 +26,18 @@ static int launch_tma_ct(const PassArgs& a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <bool FWD>
+#ifndef PFFT_PIPE_X1S
+#define PFFT_PIPE_X1S 1
+#endif
+
+template <bool FWD, bool DIRECT>
 static int launch_pipe_t(const PassArgs& a, cudaStream_t s) {
-  static const int ok = configure_kernel(reinterpret_cast<const void*>(row_pipe_kernel<FWD>));
+  constexpr bool X1S = PFFT_PIPE_X1S != 0;
+  static const int ok = configure_kernel(reinterpret_cast<const void*>(row_pipe_kernel<FWD, DIRECT, X1S>));
   if (ok != 0) return -1;
   const int total = a.LB * a.batch;
   dim3 grid(total < a.pipe_grid ? total : a.pipe_grid), block(1 << (kPipeLogL - 5));
-  row_pipe_kernel<FWD><<<grid, block, a.smem_bytes, s>>>(a);
+  row_pipe_kernel<FWD, DIRECT, X1S><<<grid, block, a.smem_bytes, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -41,9 +46,9 @@ static int launch_pipe_t(const PassArgs& a, cudaStream_t s) {
 // conjugated output, scaled).
 static int launch_pipe(const PassArgs& a, cudaStream_t s) {
   if (a.load_mode == MAP_BOX_H && a.store_mode == MAP_WS && !a.conj_in && !a.conj_out && a.scale == 1.0)
-    return launch_pipe_t<true>(a, s);
+    return (a.pipe_direct & 1) ? launch_pipe_t<true, true>(a, s) : launch_pipe_t<true, false>(a, s);
   if (a.load_mode == MAP_WS && a.store_mode == MAP_BOX_H && !a.conj_in && a.conj_out)
-    return launch_pipe_t<false>(a, s);
+    return (a.pipe_direct & 2) ? launch_pipe_t<false, true>(a, s) : launch_pipe_t<false, false>(a, s);
   return -1;
 }
 

@@ -174,3 +174,57 @@ def test_inverse_output_rounds_split_runs():
             if hi > lo:
                 assert 0 <= lo - h * HALF and hi - h * HALF <= HALF
                 assert (lo - x0) % 2 == 0 and (lo - h * HALF) % 2 == 0 and (hi - lo) % 2 == 0
+
+
+def test_single_round_exchange1_fits_s_and_x():
+    """Exchange 1 in one round (X1S): positions (q << 13) | (p << 4) | r
+    written and (r << 9) | p read through the padded region that starts at S
+    and runs into X; a bijection inside the 2^14 + 2^10 slots, with two
+    wavefronts per warp access."""
+    p = np.arange(P)
+    w = np.stack([xphys((q << 13) | (p << 4) | r) for q in range(2) for r in range(16)], axis=1)
+    rd = np.stack([xphys((r << 9) | p) for r in range(32)], axis=1)
+    for idx in (w, rd):
+        flat = idx.reshape(-1)
+        assert len(np.unique(flat)) == L and flat.max() < L + (L >> 4)
+        for wp in range(P // 32):
+            for j in range(idx.shape[1]):
+                assert wavefronts(2 * idx[32 * wp:32 * wp + 32, j]) == 2
+    assert set(w.reshape(-1)) == set(rd.reshape(-1))
+    # S holds 2^14 elements plus staging pads, X starts at a multiple of 16
+    # elements after it and holds 2^13 + 2^9: the region fits for any pad
+    for s_el in (L, L + 64 * 2, L + 4 * 4):
+        x_off = (s_el + 15) & ~15
+        assert L + (L >> 4) <= x_off + XSIZE
+
+
+@pytest.mark.parametrize("lg", [0, 1, 2, 3])
+def test_direct_forward_output_is_the_permutation(lg):
+    """Forward output from registers when the permutation multiplier is 1:
+    element p + 512 k goes to ((p mod 2^lg) << ls) + (p >> lg) + k 2^(9 - lg);
+    lanes of a warp form runs of 2^(5 - lg) consecutive positions."""
+    ls = 14 - lg
+    p = np.arange(P)
+    for k in range(32):
+        pos = ((p & ((1 << lg) - 1)) << ls) + (p >> lg) + k * (P >> lg)
+        assert (pos == pi_formula(p + P * k, lg, 1)).all()
+        for wp in range(P // 32):
+            lanes = np.sort(pos[32 * wp:32 * wp + 32])
+            runs = np.split(lanes, np.where(np.diff(lanes) != 1)[0] + 1)
+            assert min(len(r) for r in runs) >= 1 << (5 - lg)
+
+
+@pytest.mark.parametrize("lrun", [5, 9, 12, 14])
+def test_direct_inverse_output_finds_the_run(lrun):
+    """Box rows of uniform runs of 2^lrun elements (run j covers elements
+    [j 2^lrun, (j + 1) 2^lrun)): element e is stored at y_j + (e mod 2^lrun),
+    j = e >> lrun, and a warp's 32 consecutive elements stay in one run."""
+    rng = np.random.default_rng(lrun)
+    nr = L >> lrun
+    y = rng.permutation(nr) * (1 << lrun) + 7
+    e = np.arange(L)
+    slot = y[e >> lrun] + (e & ((1 << lrun) - 1))
+    assert len(np.unique(slot)) == L
+    for wp in range(L // 32):
+        j = e[32 * wp:32 * wp + 32] >> lrun
+        assert (j == j[0]).all()
