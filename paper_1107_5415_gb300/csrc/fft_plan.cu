@@ -774,6 +774,23 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
       }
     }
   }
+  // pencils of 2^10 complex64 points, 8 per tile: the persistent pipelined column pass
+  if (npen == 1 && P.dtype == PFFT_C64 && P.colp.fast && P.colp.L == (1 << kCPipeLogL) && P.colp.T == 8 &&
+      P.colp.LB == P.colp.L && P.colp.nthreads == 256 && P.colp.fast_tail == 1 && P.colp.fast_nmain == 2 &&
+      (d == 2 || d == 3) && P.nD % 8 == 0) {
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P.device) != cudaSuccess || nsm < 1)
+      return PFFT_ERR_CUDA;
+    const int stw_off = kCPipeS + kCPipeX;
+    const int bytes = (stw_off + P.colp.stw_n) * 8;
+    if (bytes <= 110 * 1024) {
+      P.colp.cpipe = 1;
+      P.colp.cpipe_x_off = kCPipeS;
+      P.colp.cpipe_grid = 2 * nsm;
+      P.colp.stw_smem_off = stw_off;
+      P.colp.smem_bytes = bytes;
+    }
+  }
   if (!idx.empty()) {
     int* didx = nullptr;
     if (int e_ = device_alloc((void**)&didx, idx.size() * sizeof(int))) return pfft_status(e_);
