@@ -7,15 +7,25 @@
 // current one.  Thread (c, p), c < 8, p < 32, holds rows p + 32 k of column
 // c (two radix-32 Stockham stages, as col_fast_ct_kernel).  Shared memory:
 //
-//   S (66 KiB)  the tile: filled with cp.async (16-byte pieces of the
-//               workspace rows in the forward direction, the sheared gather
-//               from the output box in the inverse one) in a dense
-//               [row][column] layout, read into registers, then reused as
-//               the padded exchange tile of the two stages; after the
-//               exchange the copies of the next tile are issued into it;
-//   X (32 KiB)  the sheared output of the forward direction, in two rounds
-//               of 16 walk steps;
+//   S (66 KiB)  forward: the tile, filled with cp.async in 16-byte pieces of
+//               the workspace rows (dense [row][column]); as soon as the
+//               threads have read it the copies of the next tile are issued
+//               into it.  Inverse: the second half of the sheared gather
+//               from the output box, then the padded exchange tile of the
+//               two stages, after which the next tile's second half is
+//               gathered into it;
+//   X (33 KiB)  forward: the exchange between the two stages and the
+//               sheared output, each in two rounds of half a tile.
+//               Inverse: the first half of the gather, issued for the next
+//               tile as soon as the current one has been read;
+//   Es          the column points of the walk (forward);
 //   stw         the stage twiddles.
+//
+// Exchange in two rounds.  Stage 0 writes position 32 p + r, stage 1 reads
+// p + 32 r' (10-bit positions per column).  Splitting by bit 9 xor bit 4
+// makes thread p write and read the register half H = h xor bit 4 of p in
+// round h (warp-uniform), and dropping bit 9 maps each round one-to-one onto
+// 512 rows of the half tile.
 //
 // Sheared output in two rounds.  The walk of thread (c, p) visits rows
 // i_j = (i_0 + 32 j) mod 1024, i_0 = p + c alpha mod 1024, and stores row
@@ -35,9 +45,30 @@
 
 namespace pfft {
 
+__device__ __forceinline__ void prefetch_l2(const void* gmem) {
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(gmem));
+}
+
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+
+// Exchange round with register half H (compile time): stage-0 outputs of
+// positions 32 p + r and stage-1 inputs of positions p + 32 r, r in
+// [16 H, 16 H + 16), at the 9-bit position (bit 9 dropped) in the padded
+// half tile, one padding row per 32 rows.
+template <int H>
+__device__ __forceinline__ void cpipe_x_write(const float2* v, float2* X, int p, int tcol) {
+  float2* wb = X + ct_phys<3>(32 * (p & 15)) + tcol;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) wb[ct_phys<3>(16 * H + i)] = v[16 * H + i];
+}
+template <int H>
+__device__ __forceinline__ void cpipe_x_read(float2* v, const float2* X, int p, int tcol) {
+  const float2* rb = X + ct_phys<3>(p) + tcol;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[16 * H + i] = rb[ct_phys<3>(32 * i)];
 }
 
 // FWD: the forward column pass (workspace -> box, scaled); else the inverse
@@ -59,94 +90,180 @@ __global__ void __launch_bounds__(256, 2) col_pipe_kernel(PassArgs a) {
   C* __restrict__ out_all = static_cast<C*>(a.out);
   C* stw = stage_table(S, a);
 
-  // the sheared walk of this thread: rows i0 + 32 j (mod L), box point step cP
+  // The sheared walk of thread (c, p) visits rows i0 + 32 j (mod L).  Row
+  // p + 32 k of column c (register k of this thread) is visited by the walker
+  // (c, pw), pw = (p - c alpha) mod 32, at step (k - m0h) mod 32, m0h =
+  // floor(i_0 / 32) of that walker; this thread as a walker reads residue sw.
   const int off = int((int64_t(tcol) * a.alpha[0]) % L);
   int i0 = p + off;
   if (i0 >= L) i0 -= L;
+  const int pw = (p - off) & (P - 1);
+  int i0w = pw + off;
+  if (i0w >= L) i0w -= L;
+  const int m0h = i0w >> 5;
+  const int sw = i0 & (P - 1);
 
-  auto issue = [&](int g) {
+  // The walk needs the box points of its start (a row of the column cycle,
+  // times its generator; L1-resident table entries), of its step 32 g and
+  // the point E(p0 + c) of its column.  The column points of a tile are
+  // copied into Es (double-buffered by the parity of the CTA's tile count)
+  // ahead of their use: with the tile's own copies (forward), one tile
+  // earlier still (inverse, whose gather for tile n + 1 runs during tile n).
+  int* Es = reinterpret_cast<int*>(S + a.cpipe_e_off);  // [2][T][TS]
+  auto copy_points = [&](int g, int slot) {
+    if (tid < T) {
+      const int b = g / ntile, p0 = (g - b * ntile) << LOGT;
+      if constexpr (TS == 2)
+        cp_async8(Es + (slot * T + tid) * TS, a.Etab + (size_t)(p0 + tid) * TS);
+      else
+        cp_async16(Es + (slot * T + tid) * TS, a.Etab + (size_t)(p0 + tid) * TS);
+    }
+  };
+  auto col_point = [&](int slot, int* et) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) et[r] = r < TS ? Es[(slot * T + tcol) * TS + r] : 0;
+  };
+
+  // forward: the workspace tile in 16-byte pieces, dense [row][column]
+  auto issue_fwd = [&](int g, int n) {
     const int b = g / ntile, p0 = (g - b * ntile) << LOGT;
     const C* in = in_all + (int64_t)b * a.m;
-    if constexpr (FWD) {
 #pragma unroll
-      for (int i = 0; i < (L * T / 2) / NT; ++i) {  // 16-byte pieces, dense [row][column]
-        const int c = tid + NT * i;
-        const int row = c >> 2, part = c & 3;
-        cp_async16(S + row * T + part * 2, in + (size_t)row * a.nD + p0 + part * 2);
-      }
-    } else {
-      int z[4], et[4], cP[4];
-      load_point<TS>(a.Etab, p0 + tcol, et);
-      load_point<TS>(a.Ctab, i0, z);
-      load_point<TS>(a.Ctab, P, cP);
-      box_add_t<DIM>(a.boxG, z, et);
-      int i = i0;
+    for (int i = 0; i < (L * T / 2) / NT; ++i) {
+      const int c = tid + NT * i;
+      const int row = c >> 2, part = c & 3;
+      cp_async16(S + row * T + part * 2, in + (size_t)row * a.nD + p0 + part * 2);
+    }
+    copy_points(g, n & 1);
+  };
+  // inverse: walk steps [16 h, 16 h + 16) of the sheared gather, in walk
+  // layout W[j mod 16][p][c] (word address 512 t + 16 p + 2 c: conflict free),
+  // half 0 into X, half 1 into S
+  auto issue_inv = [&](int g, int h, int n) {
+    const int b = g / ntile;
+    const C* in = in_all + (int64_t)b * a.m;
+    int z[4], cP[4], et[4];
+    col_point(n & 1, et);
+    int ih = i0 + (h << (LOGL - 1));
+    if (ih >= L) ih -= L;
+    load_point<TS>(a.Ctab, ih, z);
+    load_point<TS>(a.Ctab, P, cP);
+    box_add_t<DIM>(a.boxG, z, et);
+    C* dst = (h ? S : X) + p * T + tcol;
 #pragma unroll 4
-      for (int j = 0; j < R; ++j) {
-        cp_async8(S + i * T + tcol, in + box_slot_t<DIM>(a.boxG, z));
-        box_add_t<DIM>(a.boxG, z, cP);
-        i += P;
-        if (i >= L) i -= L;
-      }
+    for (int t = 0; t < 16; ++t) {
+      cp_async8(dst + t * NT, in + box_slot_t<DIM>(a.boxG, z));
+      box_add_t<DIM>(a.boxG, z, cP);
     }
   };
 
-  if (blockIdx.x < total) issue(blockIdx.x);
-  for (int g = blockIdx.x; g < total; g += gridDim.x) {
+  if (blockIdx.x < total) {
+    if constexpr (FWD) {
+      issue_fwd(blockIdx.x, 0);
+    } else {
+      copy_points(blockIdx.x, 0);
+      cp_async_wait_all();
+      __syncthreads();
+      issue_inv(blockIdx.x, 0, 0);
+      issue_inv(blockIdx.x, 1, 0);
+      if (blockIdx.x + gridDim.x < total) copy_points(blockIdx.x + gridDim.x, 1);
+    }
+  }
+  int n = 0;  // this CTA's tile count
+  for (int g = blockIdx.x; g < total; g += gridDim.x, ++n) {
+    const int gn = g + gridDim.x;
     cp_async_wait_all();
     __syncthreads();  // the tile (and, once, the stage table) has landed
     const int b = g / ntile, p0 = (g - b * ntile) << LOGT;
     C v[R];
+    if constexpr (FWD) {
 #pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = S[(p + P * k) * T + tcol];
-    if constexpr (!FWD) {
+      for (int k = 0; k < R; ++k) v[k] = S[(p + P * k) * T + tcol];
+      __syncthreads();  // S is read: the next tile may land in it
+      if (gn < total) issue_fwd(gn, n + 1);
+      // stage 0 (Ns = 1), exchange in two rounds through X: round h moves
+      // register half H = h xor bit 4 of p (positions 32 p + r written,
+      // p + 32 r' read, split by bit 9 xor bit 4 of the position; bit 9 dropped)
+      dft_pow2<C, R>(v);
 #pragma unroll
-      for (int k = 0; k < R; ++k) v[k] = cconj(v[k]);
-    }
-    __syncthreads();  // dense reads done: S becomes the exchange tile
-    // stage 0 (Ns = 1), exchange through the padded tile
-    dft_pow2<C, R>(v);
-    {
+      for (int h = 0; h < 2; ++h) {
+        if (h) __syncthreads();  // round 0's reads of X are done
+        if ((h ^ (p >> 4)) & 1)
+          cpipe_x_write<1>(v, X, p, tcol);
+        else
+          cpipe_x_write<0>(v, X, p, tcol);
+        __syncthreads();
+        if ((h ^ (p >> 4)) & 1)
+          cpipe_x_read<1>(v, X, p, tcol);
+        else
+          cpipe_x_read<0>(v, X, p, tcol);
+      }
+    } else {
+      // register k from walk step j = (k - m0h) mod 32 of walker pw (conjugated input)
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const int j = (k - m0h) & (R - 1);
+        const C* src = j < 16 ? X + j * NT : S + (j - 16) * NT;
+        v[k] = cconj(src[pw * T + tcol]);
+      }
+      __syncthreads();  // X and S are read: the first half of the next gather may land in X
+      if (gn < total) issue_inv(gn, 0, n + 1);
+      // stage 0 (Ns = 1), exchange through the padded tile in S
+      dft_pow2<C, R>(v);
       C* wb = S + ct_phys<LOGT>(p * R) + tcol;
 #pragma unroll
       for (int r = 0; r < R; ++r) wb[ct_phys<LOGT>(r)] = v[r];
-    }
-    __syncthreads();
-    {
+      __syncthreads();
       const C* rb = S + ct_phys<LOGT>(p) + tcol;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r] = rb[ct_phys<LOGT>(r * P)];
+      __syncthreads();  // S is free: the second half of the next gather may land in it
+      if (gn < total) {
+        issue_inv(gn, 1, n + 1);
+        const int gnn = gn + gridDim.x;
+        if (gnn < total) {
+          copy_points(gnn, n & 1);  // for the gather after next
+          // pull the lines of the gather after next into L2: row i of column
+          // p0 starts a run of T consecutive slots (the shear), four rows per thread
+          const int b2 = gnn / ntile, p2 = (gnn - b2 * ntile) << LOGT;
+          const C* in2 = in_all + (int64_t)b2 * a.m;
+          int e2[4];
+          load_point<TS>(a.Etab, p2, e2);
+#pragma unroll
+          for (int q = 0; q < L / NT; ++q) {
+            int y[4];
+            load_point<TS>(a.Ctab, tid + NT * q, y);
+            box_add_t<DIM>(a.boxG, y, e2);
+            const int y0 = box_slot_t<DIM>(a.boxG, y);
+            prefetch_l2(in2 + y0);
+            prefetch_l2(in2 + min(y0 + T - 1, a.m - 1));  // the run's end, inside the signal
+          }
+        }
+      }
     }
-    __syncthreads();  // S is free: the next tile may land in it
-    if (g + gridDim.x < total) issue(g + gridDim.x);
     // stage 1 (Ns = 32): v[r] = frequency p + 32 r
     if (p) main_twiddle<C, R>(v, stw + a.stw_off[1] + p * 5);
     dft_pow2<C, R>(v);
 
     if constexpr (FWD) {
       // sheared store in two rounds of 16 walk steps through X
-      const int pw = (p - off) & (P - 1);  // the walker of this thread's residue
-      int i0w = pw + off;
-      if (i0w >= L) i0w -= L;
-      const int m0h = i0w >> 5;
-      const int sw = i0 & (P - 1);
-      int z[4], et[4], cP[4];
-      load_point<TS>(a.Etab, p0 + tcol, et);
+      int z[4], cP[4], ec[4];
       load_point<TS>(a.Ctab, i0, z);
       load_point<TS>(a.Ctab, P, cP);
-      box_add_t<DIM>(a.boxG, z, et);
+      col_point(n & 1, ec);
+      box_add_t<DIM>(a.boxG, z, ec);
       C* out = out_all + (int64_t)b * a.m;
       const float sc = float(a.scale);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        if (h) __syncthreads();  // round 0's reads of X are done
+        __syncthreads();  // the previous reads of X are done
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int t = (r - m0h - 16 * h) & 31;
           if (t < 16) X[(t * P + p) * T + tcol] = v[r];
         }
         __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
         for (int t = 0; t < 16; ++t) {
           const C x = X[(t * P + sw) * T + tcol];
           out[box_slot_t<DIM>(a.boxG, z)] = cmake<C>(x.x * sc, x.y * sc);

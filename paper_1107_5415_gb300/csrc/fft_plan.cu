@@ -781,11 +781,13 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P.device) != cudaSuccess || nsm < 1)
       return PFFT_ERR_CUDA;
-    const int stw_off = kCPipeS + kCPipeX;
+    const int e_off = kCPipeS + kCPipeX;  // 2 x 8 column points of up to 4 int32: 32 elements
+    const int stw_off = e_off + 32;
     const int bytes = (stw_off + P.colp.stw_n) * 8;
     if (bytes <= 110 * 1024) {
       P.colp.cpipe = 1;
       P.colp.cpipe_x_off = kCPipeS;
+      P.colp.cpipe_e_off = e_off;
       P.colp.cpipe_grid = 2 * nsm;
       P.colp.stw_smem_off = stw_off;
       P.colp.smem_bytes = bytes;

@@ -40,10 +40,11 @@ constexpr int kPipeHalf = 1 << (kPipeLogL - 1);
 constexpr int kPipeX = kPipeHalf + (kPipeHalf >> 4);
 // Persistent pipelined column pass (fft_col_pipe.cuh): pencils of
 // 2^kCPipeLogL complex64 points, 8 columns per tile; shared memory holds the
-// padded tile (kCPipeS elements) and the two-round output buffer (kCPipeX).
+// tile (kCPipeS elements: room for one padding row per 32 rows) and the
+// two-round exchange and output buffer (kCPipeX: half a padded tile).
 constexpr int kCPipeLogL = 10;
-constexpr int kCPipeS = ((1 << kCPipeLogL) + (1 << (kCPipeLogL - 5))) * 8;
-constexpr int kCPipeX = 16 * 32 * 8;
+constexpr int kCPipeS = ((1 << kCPipeLogL) + (1 << (kCPipeLogL - 5))) * 8;  // padded tile
+constexpr int kCPipeX = ((1 << (kCPipeLogL - 1)) + (1 << (kCPipeLogL - 6))) * 8;
 constexpr int kMaxSub = 3;
 constexpr int kMaxThreads = 512;
 constexpr int kRadixOrder[7] = {16, 8, 4, 2, 3, 5, 7};
@@ -132,7 +133,8 @@ struct alignas(16) PassArgs {
   int pipe_direct;     // 1: output stored from registers (see fft_row_pipe.cuh)
   int pipe_lrun;       // log2 of the uniform run length of the box rows (0: runs not uniform)
   int cpipe;           // 1: use col_pipe_kernel (fft_col_pipe.cuh)
-  int cpipe_x_off;     // element offset of its output buffer in shared memory
+  int cpipe_x_off;     // element offset of its exchange / output buffer in shared memory
+  int cpipe_e_off;     // element offset of its column-point buffer (2 x 8 x 4 int32)
   int cpipe_grid;      // CTAs of its launch (two per SM)
   // workspace-order staging of the TMA row pass in 2^pi_lg blocks of 2^pi_lspan
   // positions, each followed by stg_pad elements (0: one dense block), so that

@@ -4,8 +4,10 @@ p + 32 k of column c).
 
 The model replays every shared-memory access of the kernel for one tile:
 
-* the dense tile read, the radix-32 stage, the exchange through the padded
-  tile and the twiddled second stage give each column's 1024-point DFT
+* the dense tile read, the radix-32 stage, the exchange in two rounds
+  through the padded half tile X (round h moves register half
+  h xor bit 4 of p) and the twiddled second stage give each column's
+  1024-point DFT
   (numpy), v[r] of thread (c, p) = frequency p + 32 r;
 * in the two output rounds each slot of X is written once, and the walker
   (c, p) reads at step j exactly the frequency i_j = (p + c alpha + 32 j)
@@ -56,19 +58,28 @@ def model(tile, alpha, check=True):
         if check:
             check_banks(idx)
     v = np.fft.fft(v, axis=1)  # stage 0 (Ns = 1): output r at position 32 p + r
-    S = np.full(ct_phys(L), np.nan + 0j)
-    for r in range(R):
-        idx = ct_phys(p * R) + ct_phys(r) + c
-        assert (ct_phys(p * R + r) + c == idx).all()
-        S[idx] = v[:, r]
+    # exchange in two rounds through the padded half tile X: round h moves
+    # register half H = h xor bit 4 of p; bit 9 of the position is dropped
+    XS = ct_phys(L // 2)
+    for h in range(2):
+        X = np.full(XS, np.nan + 0j)
+        H = h ^ ((p >> 4) & 1)
+        regs = 16 * H[:, None] + np.arange(16)[None, :]
+        widx = ct_phys(32 * (p & 15))[:, None] + ct_phys(regs) + c[:, None]
+        pos_w = 32 * p[:, None] + regs
+        assert (((pos_w >> 9) ^ (pos_w >> 4)) & 1 == h).all()
+        assert (widx == ct_phys(pos_w & 511) + c[:, None]).all()
+        assert len(np.unique(widx)) == widx.size and widx.max() < XS
+        X[widx] = v[tid[:, None], regs]
+        ridx = ct_phys(p)[:, None] + ct_phys(32 * np.arange(16))[None, :] + c[:, None]
+        pos_r = p[:, None] + 32 * regs
+        assert (((pos_r >> 9) ^ (pos_r >> 4)) & 1 == h).all()
+        assert (ridx == ct_phys(pos_r & 511) + c[:, None]).all()
+        v[tid[:, None], regs] = X[ridx]
         if check:
-            check_banks(idx)
-    for r in range(R):
-        idx = ct_phys(p) + ct_phys(r * P) + c
-        assert (ct_phys(p + r * P) + c == idx).all()
-        v[:, r] = S[idx]
-        if check:
-            check_banks(idx)
+            for j in range(16):
+                check_banks(widx[:, j])
+                check_banks(ridx[:, j])
     assert not np.isnan(v).any()
     v *= np.exp(-2j * np.pi * np.outer(p, np.arange(R)) / L)
     v = np.fft.fft(v, axis=1)  # v[r] = frequency p + 32 r
@@ -134,8 +145,54 @@ def test_forward_loads_cover_the_tile_aligned():
 
 
 def test_shared_memory_layout_fits_two_ctas_per_sm():
-    S = ct_phys(L)
-    X = 16 * P * T
+    S = L * T
+    X = max(ct_phys(L // 2), 16 * P * T)
+    Es = 2 * T * 4 * 4 // 8  # two tiles' column points, 4 int32 each, in 8-byte elements
     stw_n = 166
-    per_cta = (S + X + stw_n) * 8
-    assert S >= L * T and per_cta <= 110 * 1024 and 2 * (per_cta + 1024) <= 228 * 1024
+    per_cta = (ct_phys(L) + X + Es + stw_n) * 8
+    assert ct_phys(L) >= S and Es == 32 and per_cta <= 110 * 1024 and 2 * (per_cta + 1024) <= 228 * 1024
+
+
+def test_single_round_exchange_through_the_padded_tile():
+    """The inverse direction exchanges in one round through S: positions
+    32 p + r written and p + 32 r read at ct_phys(position) + c, a bijection
+    onto the padded tile that fits the tile buffer, two wavefronts per warp."""
+    tid = np.arange(256)
+    c, p = tid & 7, tid >> 3
+    w = np.stack([ct_phys(32 * p + r) + c for r in range(R)], axis=1)
+    rd = np.stack([ct_phys(p + 32 * r) + c for r in range(R)], axis=1)
+    for idx in (w, rd):
+        assert len(np.unique(idx)) == L * T and idx.max() < ct_phys(L)
+        for j in range(R):
+            check_banks(idx[:, j])
+    assert set(w.reshape(-1)) == set(rd.reshape(-1))
+
+
+@pytest.mark.parametrize("alpha", [0, 3, 96, 513])
+def test_inverse_gather_in_walk_layout(alpha):
+    """Inverse direction: walker (c, p) gathers step j = 16 h + t of its walk
+    (row (i_0 + 32 j) mod 1024 of column c) into W_h[t][p][c] (h = 0: X,
+    h = 1: S); thread (c, p) then finds its register k (row p + 32 k) at
+    step j = (k - m0h) mod 32 of walker pw = (p - c alpha) mod 32 -- every
+    register once, every access conflict free."""
+    tid = np.arange(256)
+    c, p = tid & 7, tid >> 3
+    off = (c * alpha) % L
+    i0 = (p + off) % L
+    W = np.full((2, 16, P, T), -1, np.int64)
+    for j in range(32):
+        h, t = divmod(j, 16)
+        rows = (i0 + 32 * j) % L
+        assert (W[h, t, p, c] == -1).all()
+        W[h, t, p, c] = rows * T + c  # the tile element gathered
+        if alpha in (3, 513):
+            check_banks(((t * P + p) * T + c))
+    pw = (p - off) & (P - 1)
+    m0h = ((pw + off) % L) >> 5
+    for k in range(R):
+        j = (k - m0h) & 31
+        h, t = j // 16, j % 16
+        got = W[h, t, pw, c]
+        assert (got == (p + P * k) * T + c).all()
+        if alpha in (3, 513):
+            check_banks((t * P + pw) * T + c)
