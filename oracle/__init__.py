@@ -321,3 +321,87 @@ def merge_general(M, J, symbols, parts):
     for t in range(p):
         c[:, S[:, t]] = vals[:, :, t]
     return c
+
+
+# ----------------------------------------------------------------------------
+# Dilations of any prime |det J| = p (Section 5.3, step 4 with p bands)
+# ----------------------------------------------------------------------------
+def pattern_generator_J(J, l):
+    """u = J z for the generator z of the cyclic pattern P(J) = Lambda(J) cap
+    [-1/2, 1/2)^d dual to the generator l of G(J^T): l^T z = 1/p (mod 1),
+    p = |det J|.  For p = 2 this is the non-zero point of ``wavelet_shift``."""
+    p = abs(L.det(J))
+    inv = L.inverse(J)
+    for y in L.box_points(L.hnf(J)):
+        z = L.matvec(inv, list(y))
+        frac = sum(Fraction(a) * b for a, b in zip(l, z))
+        if (frac - Fraction(1, p)).denominator == 1:
+            zc = [x - (x + Fraction(1, 2)).__floor__() for x in z]
+            return [int(x) for x in L.matvec(J, zc)]
+    raise ValueError("no pattern point of J pairs with l to 1/p")
+
+
+def householder_completion(u):
+    """Real orthogonal, symmetric p x p matrix with first row (and column) u,
+    for a unit vector u with u_0 >= 0: U = 2 v v^T / (v^T v) - I, v = u + e_0
+    (the negated reflection that exchanges e_0 and -u; v^T v = 2 + 2 u_0 > 0,
+    so U is defined for every such u, and for p = 2 its second row is
+    (u_1, -u_0))."""
+    u = np.asarray(u, dtype=np.float64)
+    p = len(u)
+    v = u.copy()
+    v[0] += 1.0
+    return 2.0 * np.outer(v, v) / float(v @ v) - np.eye(p)
+
+
+def dirichlet_p_symbols(M, J):
+    """Symbol system of a dilation of prime determinant p with cyclic G(J^T)
+    (this project's reading of Section 5.3 step 4 for p bands):
+
+    * scaling symbol A(h) = sqrt(p w(N^{-T} h)), the periodised Dirichlet
+      weight of Section 6.2 (``scaling_symbol``), so sum_fibre |A|^2 = p;
+    * on the fibre h_t = g + t N^T l (t < p) of g in the box of H(N^T), with
+      u_t = A(h_t) / sqrt(p) and U the Householder completion of u, the band
+      symbols b_j(h_t) = sqrt(p) U[j, t] e(g)^j, j < p, with
+      e(g) = exp(-2 pi i g^T N^{-1} z) for the generator z of P(J) dual to l.
+
+    b_0 = A, and (b_j(h_t) / sqrt(p))_{j,t} is unitary on every fibre; for
+    p = 2 the system is the scaling / wavelet pair of Section 6.2.
+    Returns symbols [p, |det M|] on the box of H(M^T)."""
+    M = [list(map(int, r)) for r in M]
+    J = [list(map(int, r)) for r in J]
+    S, p, n = _general_fibres(M, J)
+    m = n * p
+    HM = L.hnf(L.transpose(M))
+    hs = np.array([L.point_of(HM, s) for s in range(m)], dtype=np.int64)
+    A = scaling_symbol(M, J, hs, DIRICHLET)
+    l = cyclic_generator_JT(J)
+    u = pattern_generator_J(J, l)
+    adj = L.adjugate(M)
+    D = L.det(M)
+    sgn = 1 if D > 0 else -1
+    # exact phase numerator of g^T M^{-1} u = sgn g^T adj(M) u / m
+    au = [sum(adj[r][c] * u[c] for c in range(len(u))) for r in range(len(u))]
+    sym = np.zeros((p, m), dtype=np.complex128)
+    HN = L.hnf(L.transpose(exact_N(M, J)))
+    for gs in range(n):
+        g = L.point_of(HN, gs)
+        num = (sgn * sum(a * b for a, b in zip(g, au))) % m
+        e = np.exp(-2j * np.pi * num / m)
+        U = householder_completion(A[S[gs]] / np.sqrt(p))
+        for j in range(p):
+            sym[j, S[gs]] = np.sqrt(p) * U[j] * e ** j
+    return sym
+
+
+def wavelet_level_p(M, J, c_hat=None, parts=None, mode="decompose"):
+    """One split level by a dilation of prime determinant p with the symbol
+    system of ``dirichlet_p_symbols``: Section 5.3 step 4 (``split_general``),
+    and its inverse, which is the adjoint (``merge_general``) because the
+    system is unitary on every fibre.
+    decompose: c_hat [batch, m] -> parts [p, batch, m / p];
+    reconstruct: parts -> c_hat."""
+    sym = dirichlet_p_symbols(M, J)
+    if mode == "decompose":
+        return split_general(M, J, sym, c_hat)
+    return merge_general(M, J, sym, parts)

@@ -102,40 +102,67 @@ def uneven_mix(n_patterns: int = 4096, seed: int = 4, max_det: int = 1 << 20,
     return out
 
 
-def parity_dilation(M):
-    """A dilation J with |det J| = 2 and J^{-1} M integral, for an integer
-    matrix M of even determinant (workload construction, not part of the
-    method).  J Z^d = {x : v . x even} for a non-zero v in {0,1}^d with
-    v^T M = 0 mod 2 (one exists: M mod 2 is singular).  With r the last index
-    where v_r = 1, the columns e_j - v_j e_r (j != r) and 2 e_r span that
-    lattice: J = I + e_r w^T, w_j = -v_j (j != r), w_r = 1."""
+def prime_dilation(M, p: int):
+    """A dilation J with |det J| = p (a prime dividing det M) and J^{-1} M
+    integral (workload construction, not part of the method).
+    J Z^d = {x : v . x = 0 mod p} for a non-zero v in GF(p)^d with
+    v^T M = 0 mod p (one exists: M mod p is singular), scaled so that its last
+    non-zero entry v_r is 1.  The columns e_j - v_j e_r (j != r) and p e_r
+    span that lattice: J = I + e_r w^T, w_j = -v_j (j != r), w_r = p - 1."""
     d = len(M)
-    A = [[int(M[i][j]) & 1 for i in range(d)] for j in range(d)]  # rows of M^T mod 2
-    # null vector of M^T over GF(2) by elimination (d <= 4: plain loops)
-    piv_cols, rows = [], [r[:] for r in A]
-    rank = 0
+    rows = [[int(M[i][j]) % p for i in range(d)] for j in range(d)]  # rows of M^T mod p
+    piv_cols, rank = [], 0
     for c in range(d):
-        p = next((r for r in range(rank, d) if rows[r][c]), None)
-        if p is None:
+        q = next((r for r in range(rank, d) if rows[r][c]), None)
+        if q is None:
             continue
-        rows[rank], rows[p] = rows[p], rows[rank]
+        rows[rank], rows[q] = rows[q], rows[rank]
+        inv = pow(rows[rank][c], p - 2, p)
+        rows[rank] = [(x * inv) % p for x in rows[rank]]
         for r in range(d):
             if r != rank and rows[r][c]:
-                rows[r] = [a ^ b for a, b in zip(rows[r], rows[rank])]
+                f = rows[r][c]
+                rows[r] = [(a - f * b) % p for a, b in zip(rows[r], rows[rank])]
         piv_cols.append(c)
         rank += 1
     free = [c for c in range(d) if c not in piv_cols]
     if not free:
-        raise ValueError("det M is odd: no dilation of determinant 2 divides M")
+        raise ValueError(f"{p} does not divide det M: no dilation of determinant {p} divides M")
     v = [0] * d
     v[free[0]] = 1
     for i, c in enumerate(piv_cols):
-        v[c] = rows[i][free[0]]
+        v[c] = (-rows[i][free[0]]) % p
     r = max(i for i in range(d) if v[i])
+    inv = pow(v[r], p - 2, p)
+    v = [(x * inv) % p for x in v]
     J = [[int(i == j) for j in range(d)] for i in range(d)]
     for j in range(d):
-        J[r][j] = 2 if j == r else -v[j]
+        J[r][j] = p if j == r else -v[j]
     return J
+
+
+def parity_dilation(M):
+    """A dilation J with |det J| = 2 and J^{-1} M integral: prime_dilation(M, 2)."""
+    return prime_dilation(M, 2)
+
+
+def smallest_prime_factor(n: int) -> int:
+    n = abs(int(n))
+    f = 2
+    while f * f <= n:
+        if n % f == 0:
+            return f
+        f += 1
+    return n
+
+
+def mix_dilation(M):
+    """The dilation of the uneven mix: determinant 2 when det M is even, else
+    the smallest (odd) prime p dividing det M."""
+    D = 1
+    for r in range(len(M)):
+        D *= int(M[r][r])  # upper triangular
+    return prime_dilation(M, smallest_prime_factor(D))
 
 
 def random_regular_matrix(rng, d: int, amax: int, max_det: int):

@@ -574,3 +574,103 @@ def test_wavelet_part_of_a_delta_matches_the_symbol_definition(M, name):
         assert abs(d2[s, g] - np.conj(B) / math.sqrt(2)) < 1e-13, (h, d2[s, g], B)
         others = np.delete(d2[s], g)
         assert np.abs(others).max(initial=0.0) == 0.0
+
+
+# ------------------------------------------- dilations of prime determinant p
+P_CASES = [([[9, 0], [0, 9]], [[3, 0], [0, 1]]), ([[9, 3], [0, 9]], [[1, 0], [0, 3]]),
+           ([[15, 5], [0, 10]], [[1, 0], [0, 5]]), ([[9, 6], [9, 15]], [[1, 0], [-2, 3]]),
+           ([[6, 1, 2], [0, 7, 3], [0, 0, 14]], [[1, 0, 0], [0, 1, 0], [0, 0, 7]]),
+           ([[10, 0, 0], [0, 10, 0], [0, 0, 5]], [[5, 0, 0], [0, 1, 0], [0, 0, 1]])]
+
+
+def _p_fibres(M, J):
+    return oracle._general_fibres(M, J)
+
+
+@pytest.mark.parametrize("M,J", P_CASES)
+def test_prime_dilation_scaling_weights_sum_to_p(M, J):
+    """sum over each fibre of |A|^2 = p for the periodised Dirichlet symbol:
+    the p members of a fibre cover every Z^d shift of N^{-T} g once, and the
+    box indicator (1/2 on the boundary) is a partition of unity."""
+    S, p, n = _p_fibres(M, J)
+    HM = L.hnf(L.transpose(M))
+    hs = np.array([L.point_of(HM, s) for s in range(n * p)])
+    A = oracle.scaling_symbol(M, J, hs, oracle.DIRICHLET)
+    assert np.allclose((A[S] ** 2).sum(axis=1), p, atol=1e-13)
+    assert (A >= 0).all()
+
+
+def test_prime_dilation_two_scale_relation():
+    """c_k(phi_N) = A_h c_k(phi_M) (Section 6.2) for J = diag(3, 1) on
+    M = 9 I, where [-1/2,1/2]^2 lies inside J^T [-1/2,1/2]^2."""
+    M, J = [[9, 0], [0, 9]], [[3, 0], [0, 1]]
+    N = oracle.exact_N(M, J)
+    ks = _closed_cube_reps(M)
+    A = oracle.scaling_symbol(M, J, np.array(ks), oracle.DIRICHLET)
+    for k, a in zip(ks, A):
+        assert abs(_dirichlet_coeff(N, k) - a * _dirichlet_coeff(M, k)) < 1e-14
+
+
+@pytest.mark.parametrize("u", [[1, 0, 0], [0, 1, 0], [0.6, 0.8, 0], [0.5, 0.5, 0.5, 0.5], [0, 0, 0, 0, 1],
+                               [np.sqrt(0.5), 0, np.sqrt(0.5)]])
+def test_householder_completion(u):
+    """U is real orthogonal and symmetric with first row u; for p = 2 its
+    second row is (u_1, -u_0)."""
+    U = oracle.householder_completion(np.array(u, dtype=float))
+    p = len(u)
+    assert np.allclose(U @ U.T, np.eye(p), atol=1e-14)
+    assert np.allclose(U, U.T, atol=1e-14)
+    assert np.allclose(U[0], u, atol=1e-14)
+    if p == 2:
+        assert np.allclose(U[1], [u[1], -u[0]], atol=1e-14)
+
+
+@pytest.mark.parametrize("M,J", P_CASES)
+def test_prime_dilation_split_is_unitary(M, J):
+    """The p-band system is unitary on every fibre: perfect reconstruction,
+    norm preservation, orthogonal synthesised bands, band 0 = the scaling
+    part (analysis with conj(A))."""
+    S, p, n = _p_fibres(M, J)
+    m = n * p
+    sym = oracle.dirichlet_p_symbols(M, J)
+    for gs in range(n):
+        B = sym[:, S[gs]] / np.sqrt(p)
+        assert np.allclose(B @ B.conj().T, np.eye(p), atol=1e-12)
+    c = _rand_c(m, 2, 9)
+    parts = oracle.wavelet_level_p(M, J, c_hat=c)
+    assert np.allclose(np.linalg.norm(parts, axis=(0, 2)), np.linalg.norm(c, axis=1), rtol=1e-13)
+    back = oracle.wavelet_level_p(M, J, parts=parts, mode="reconstruct")
+    assert np.allclose(back, c, atol=1e-12)
+    synth = []
+    for j in range(p):
+        z = np.zeros_like(parts)
+        z[j] = parts[j]
+        synth.append(oracle.wavelet_level_p(M, J, parts=z, mode="reconstruct"))
+    for i in range(p):
+        for j in range(i + 1, p):
+            assert abs(np.vdot(synth[i], synth[j])) < 1e-12 * np.linalg.norm(c) ** 2
+    A = oracle.scaling_symbol(M, J, np.array([L.point_of(L.hnf(L.transpose(M)), s) for s in range(m)]),
+                              oracle.DIRICHLET)
+    assert np.allclose(parts[0], (c[:, S] * A[S][None]).sum(axis=2) / np.sqrt(p), atol=1e-12)
+
+
+@pytest.mark.parametrize("M,J", [([[8, 8], [-8, 8]], SI.J_DIAG_A), ([[6, 2], [-2, 6]], SI.J_DIAG_A),
+                                 ([[8, 0], [0, 8]], [[2, 0], [0, 1]]), ([[3, 1], [1, 3]], [[1, 0], [-1, 2]])])
+def test_prime_dilation_system_reduces_to_the_p2_split(M, J):
+    """For p = 2 the p-band system is the scaling / wavelet pair of Section
+    6.2 (the dedicated two-band routine)."""
+    c = _rand_c(abs(L.det(M)), 2, 4)
+    parts = oracle.wavelet_level_p(M, J, c_hat=c)
+    d1, d2 = oracle.wavelet_level(M, J, oracle.DIRICHLET, c_hat=c)
+    assert np.allclose(parts[0], d1, atol=1e-12) and np.allclose(parts[1], d2, atol=1e-12)
+
+
+@pytest.mark.parametrize("M,J", P_CASES)
+def test_pattern_generator_pairs_to_one_over_p(M, J):
+    """u = J z with z in Lambda(J) cap [-1/2, 1/2)^d and l^T z = 1/p mod 1."""
+    p = abs(L.det(J))
+    l = oracle.cyclic_generator_JT(J)
+    u = oracle.pattern_generator_J(J, l)
+    z = L.matvec(L.inverse(J), u)
+    assert all(Fraction(-1, 2) <= x < Fraction(1, 2) for x in z)
+    assert (sum(Fraction(a) * b for a, b in zip(l, z)) - Fraction(1, p)).denominator == 1
