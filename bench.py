@@ -489,13 +489,14 @@ def bench_snf_layout(pf, torch, x, ms_box, steps=50, warmup=5):
 
 def bench_mix(pf, torch, peaks_hbm, steps=10, warmup=3, n_patterns=None):
     """Uneven serving-style mix: 4096 seeded patterns (d in {2, 3}, upper
-    triangular, diagonals in [16, 512], det <= 2^20 and even), forward
-    transform + one Dirichlet split level per pattern (dilation from the
-    pattern's parity), replayed as one CUDA graph with the autotuned schedule.
-    Inputs: seeded complex normal values drawn on the device."""
+    triangular, diagonals in [16, 512], det <= 2^20), forward transform + one
+    Dirichlet split level per pattern (a dilation of determinant 2 when det M
+    is even, else of the smallest odd prime of det M with the built-in band
+    system), replayed as one CUDA graph with the autotuned schedule.  Inputs:
+    seeded complex normal values drawn on the device."""
     w = SI.WORKLOADS["uneven_mix"]
     Ms = SI.uneven_mix(w["n_patterns"], seed=w["seed"], even_det=w["even_det"])[:n_patterns or w["n_patterns"]]
-    Js = [SI.parity_dilation(M) for M in Ms]
+    Js = [SI.mix_dilation(M) for M in Ms]
     t0 = time.perf_counter()
     B = pf.PatternBatch(Ms, Js, pf.PWT_DIRICHLET, flags=pf.PFFT_BATCH_AUTOTUNE)
     t_plan = time.perf_counter() - t0
@@ -503,10 +504,12 @@ def bench_mix(pf, torch, peaks_hbm, steps=10, warmup=3, n_patterns=None):
     gen.manual_seed(w["seed"])
     x = torch.randn(B.total, dtype=torch.complex64, device="cuda", generator=gen) * math.sqrt(2.0)
     chat = torch.empty_like(x)
-    sc = torch.empty(B.total // 2, dtype=torch.complex64, device="cuda")
-    wv = torch.empty_like(sc)
+    sc = torch.empty(B.sc_total, dtype=torch.complex64, device="cuda")
+    wv = torch.empty(B.wv_total, dtype=torch.complex64, device="cuda")
     stream = torch.cuda.current_stream()
-    out = {"workload": f"uneven mix: {B.n} patterns, forward FFT + one split level each", "patterns": B.n,
+    odd = int((B.p % 2 == 1).sum())
+    out = {"workload": f"uneven mix: {B.n} patterns ({odd} of odd determinant, split by an odd prime), "
+                       "forward FFT + one split level each", "patterns": B.n,
            "points": int(B.total), "plan_s": t_plan, "schedule": dict(zip(("row_budget", "col_budget", "order", "max_radix"),
                                                                            B.schedule()))}
     for split, name in ((True, "fft_split"), (False, "fft_only")):

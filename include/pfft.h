@@ -257,25 +257,36 @@ pfft_status pwt_adjoint(pwt_plan p, const void* scaling, const void* const* wave
 pfft_status pwt_plan_destroy(pwt_plan p);
 
 /* General split step (Section 5.3, step 4) for a dilation J of any
- * determinant p = |det J| <= 16 whose group G(J^T) = Z^d / J^T Z^d is cyclic
- * (one elementary divisor of J above 1), with the p symbols supplied by the
- * caller (step 1 of the algorithm computes them from the generating
- * functions; the paper defines Dirichlet-type symbols only for |det J| = 2).
- * M = J N must hold with N integral.  For every g in G(N^T) (box of H(N^T))
- * and its fibre h_t = g + t N^T l (t < p, l a generator of G(J^T)):
- *     parts[j][b][g] = p^{-1/2} sum_t conj(symbols[j][h_t]) c_hat[b][h_t],  j < p.
- * symbols: device [p][|det M|] on the box of H(M^T); c_hat: device
- * [batch][|det M|]; parts: device [p][batch][|det M| / p].  Plan-free: the
- * exact setup runs on the host per call, the kernel is queued on `stream`.
- * Errors: PFFT_ERR_NOT_INTEGRAL (J^{-1} M), PFFT_ERR_UNSUPPORTED (p > 16 or
- * G(J^T) not cyclic), PFFT_ERR_OVERFLOW (|det M| >= 2^30), and the argument
- * errors of pfft_plan_create. */
+ * determinant p = |det J| whose group G(J^T) = Z^d / J^T Z^d is cyclic (one
+ * elementary divisor of J above 1).  M = J N must hold with N integral.  For
+ * every g in G(N^T) (box of H(N^T)) and its fibre h_t = g + t N^T l (t < p,
+ * l a generator of G(J^T)):
+ *     parts[j][b][g] = p^{-1/2} sum_t conj(b_j(h_t)) c_hat[b][h_t],  j < p.
+ * Symbols b_j:
+ *   symbols != NULL: supplied by the caller (step 1 of the algorithm
+ *     computes them from the generating functions), device [p][|det M|] on
+ *     the box of H(M^T), p <= 16;
+ *   symbols == NULL: the built-in unitary band system (p prime, up to
+ *     2^20; the paper defines Dirichlet symbols for |det J| = 2 only):
+ *     b_0 = the periodised Dirichlet scaling symbol A = sqrt(p w(N^{-T} h))
+ *     of Section 6.2, and on each fibre, labelled by the generator l = the
+ *     first unit vector outside J^T Z^d, b_j(h_t) = sqrt(p) U[j][t] e^j with
+ *     U the real orthogonal completion U = 2 V V^T / (V^T V) - I,
+ *     V = A / sqrt(p) + e_0, and e = exp(-2 pi i g^T N^{-1} z), z the
+ *     centred generator of P(J) with l^T z = 1/p.  For p = 2 this is the
+ *     pair of pwt_decompose with PWT_DIRICHLET; pwt_merge_general inverts it.
+ * c_hat: device [batch][|det M|]; parts: device [p][batch][|det M| / p].
+ * Plan-free: the exact setup runs on the host per call, the kernel is queued
+ * on `stream`.  Errors: PFFT_ERR_NOT_INTEGRAL (J^{-1} M), PFFT_ERR_UNSUPPORTED
+ * (p above the limit or G(J^T) not cyclic), PFFT_ERR_OVERFLOW
+ * (|det M| >= 2^30), and the argument errors of pfft_plan_create. */
 pfft_status pwt_split_general(int d, const int64_t* M, const int64_t* J, int64_t batch, int dtype,
                               const void* symbols, const void* c_hat, void* parts, void* stream);
 
-/* Adjoint of pwt_split_general: c_hat[b][h_t] = p^{-1/2} sum_j symbols[j][h_t]
- * parts[j][b][g].  It inverts pwt_split_general when the matrix
- * (symbols[j][h_t] / sqrt(p))_{j,t} is unitary on every fibre. */
+/* Adjoint of pwt_split_general: c_hat[b][h_t] = p^{-1/2} sum_j b_j(h_t)
+ * parts[j][b][g] (symbols as for pwt_split_general, NULL for the built-in
+ * system).  It inverts pwt_split_general when the matrix (b_j(h_t) /
+ * sqrt(p))_{j,t} is unitary on every fibre, as the built-in system is. */
 pfft_status pwt_merge_general(int d, const int64_t* M, const int64_t* J, int64_t batch, int dtype,
                               const void* symbols, const void* parts, void* c_hat, void* stream);
 
@@ -283,21 +294,27 @@ pfft_status pwt_merge_general(int d, const int64_t* M, const int64_t* J, int64_t
  * Batches of many patterns of uneven size (serving-style mixes).
  *
  * One object holds n patterns M_0 .. M_{n-1} (each with its own d_i) and
- * optionally one dilation J_i per pattern (|det J_i| = 2, J_i^{-1} M_i
- * integral).  pfft_batch_forward computes, for every pattern, the transform
- * of pfft_forward and, when dilations were given, one split level of
- * pwt_decompose with the batch's symbol (Section 5.3, step 4).  All patterns
- * run together: three grouped launches (the row pass of every pattern, the
- * column pass, the split), each CTA finding its pattern in a device table,
- * with patterns grouped by shared-memory footprint into concurrent launches,
- * replayed as one CUDA graph.
+ * optionally one dilation J_i per pattern (J_i^{-1} M_i integral, G(J_i^T)
+ * cyclic of order p_i = |det J_i|: 2, or a prime up to 2^20).  pfft_batch_forward
+ * computes, for every pattern, the transform of pfft_forward and, when
+ * dilations were given, one split level (Section 5.3, step 4): for p_i = 2
+ * the split of pwt_decompose with the batch's symbol, for p_i > 2 the
+ * built-in band system of pwt_split_general (symbols NULL; PWT_DIRICHLET
+ * only, else PFFT_ERR_UNSUPPORTED).  All patterns run together: grouped
+ * launches (the row pass of every pattern, the column pass, the split
+ * levels), each CTA finding its pattern in a device table, with patterns
+ * grouped by shared-memory footprint into concurrent launches, replayed as
+ * one CUDA graph.
  *
  * Data: the signals are concatenated, pattern i occupying elements
  * [off_i, off_i + m_i) of `in` and `c_hat`, off_i = m_0 + ... + m_{i-1},
- * m_i = |det M_i|, each in the box layout of its own plan.  The split parts of
- * pattern i occupy [off_i / 2, off_i / 2 + m_i / 2) of `scaling` and of
- * `wavelet` (every m_i is even when dilations are given).  One signal per
- * pattern (batch 1).
+ * m_i = |det M_i|, each in the box layout of its own plan.  With n_i =
+ * m_i / p_i, the scaling part of pattern i occupies [s_i, s_i + n_i) of
+ * `scaling` and its p_i - 1 band parts occupy [w_i + (j - 1) n_i,
+ * w_i + j n_i), j = 1 .. p_i - 1, of `wavelet`, where s_i = n_0 + ... +
+ * n_{i-1} and w_i = (p_0 - 1) n_0 + ... + (p_{i-1} - 1) n_{i-1}
+ * (pfft_batch_split_layout returns them; when every p_i = 2,
+ * s_i = w_i = off_i / 2).  One signal per pattern (batch 1).
  * ------------------------------------------------------------------------- */
 enum {
   PFFT_BATCH_NO_GRAPH = 1u, /* queue the grouped launches directly instead of replaying a graph */
@@ -319,6 +336,13 @@ pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, const int64_
 /* m: host array of n (|det M_i|) or NULL; total: sum of m_i or NULL. */
 pfft_status pfft_batch_info(pfft_batch b, int64_t* m, int64_t* total);
 
+/* Split layout of a batch with dilations: per pattern p_i = |det J_i| and the
+ * element offsets s_i, w_i of its scaling and band parts (see above), and
+ * the element counts of the scaling and wavelet buffers.  Host arrays of n
+ * values or NULL; without dilations every value is 0. */
+pfft_status pfft_batch_split_layout(pfft_batch b, int* p, int64_t* scaling_off, int64_t* wavelet_off,
+                                    int64_t* scaling_total, int64_t* wavelet_total);
+
 /* The chosen schedule: element budgets of the row- and column-pass tiles, the
  * launch order (1: largest work first, 0: pattern order) and the largest
  * power-of-two radix of the stages (16 or 8).  NULLs allowed. */
@@ -326,7 +350,7 @@ pfft_status pfft_batch_schedule(pfft_batch b, int* row_budget, int* col_budget, 
 
 /* in -> c_hat for every pattern; if the batch has dilations and scaling and
  * wavelet are non-NULL, also c_hat -> (scaling, wavelet).  Device pointers,
- * layout above.  The graph is built on the first call and rebuilt when any
+ * layout above (scaling / wavelet hold the totals of pfft_batch_split_layout).  The graph is built on the first call and rebuilt when any
  * of the four pointers changes; a batch may be used from one stream at a
  * time (its workspace is shared). */
 pfft_status pfft_batch_forward(pfft_batch b, const void* in, void* c_hat, void* scaling, void* wavelet,

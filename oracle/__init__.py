@@ -354,44 +354,93 @@ def householder_completion(u):
     return 2.0 * np.outer(v, v) / float(v @ v) - np.eye(p)
 
 
-def dirichlet_p_symbols(M, J):
-    """Symbol system of a dilation of prime determinant p with cyclic G(J^T)
-    (this project's reading of Section 5.3 step 4 for p bands):
+def band_generator_JT(J):
+    """The generator l = e_i of G(J^T) that labels the members of a fibre in
+    the band system: the first unit vector outside J^T Z^d (for |det J| = 2
+    the class of ``nonzero_class_JT``)."""
+    return nonzero_class_JT(J)
 
-    * scaling symbol A(h) = sqrt(p w(N^{-T} h)), the periodised Dirichlet
-      weight of Section 6.2 (``scaling_symbol``), so sum_fibre |A|^2 = p;
-    * on the fibre h_t = g + t N^T l (t < p) of g in the box of H(N^T), with
-      u_t = A(h_t) / sqrt(p) and U the Householder completion of u, the band
-      symbols b_j(h_t) = sqrt(p) U[j, t] e(g)^j, j < p, with
-      e(g) = exp(-2 pi i g^T N^{-1} z) for the generator z of P(J) dual to l.
 
-    b_0 = A, and (b_j(h_t) / sqrt(p))_{j,t} is unitary on every fibre; for
-    p = 2 the system is the scaling / wavelet pair of Section 6.2.
-    Returns symbols [p, |det M|] on the box of H(M^T)."""
+def band_fibre_slots(M, J, gslots):
+    """Slots (box of H(M^T)) of the members h_t = g + t N^T l, t < p, of the
+    fibres of the given slots g of the box of H(N^T), l = band_generator_JT(J)."""
+    N = exact_N(M, J)
+    p = abs(L.det(J))
+    HM, HN = L.hnf(L.transpose(M)), L.hnf(L.transpose(N))
+    shift = L.matvec(L.transpose(N), band_generator_JT(J))
+    out = np.empty((len(gslots), p), dtype=np.int64)
+    for i, gs in enumerate(gslots):
+        g = L.point_of(HN, int(gs))
+        for t in range(p):
+            out[i, t] = L.slot_of(HM, L.box_reduce(HM, [a + t * b for a, b in zip(g, shift)]))
+    return out
+
+
+def _band_system_at(M, J, gslots):
+    """Members and symbols of the fibres of the slots gslots of the box of
+    H(N^T): (S [n, p] member slots, b [n, p(band), p(member)] values of
+    b_j(h_t)); see ``dirichlet_p_symbols``."""
     M = [list(map(int, r)) for r in M]
     J = [list(map(int, r)) for r in J]
-    S, p, n = _general_fibres(M, J)
-    m = n * p
+    N = exact_N(M, J)
+    p = abs(L.det(J))
+    m = abs(L.det(M))
+    gslots = np.asarray(list(gslots), dtype=np.int64)
+    S = band_fibre_slots(M, J, gslots)
     HM = L.hnf(L.transpose(M))
-    hs = np.array([L.point_of(HM, s) for s in range(m)], dtype=np.int64)
-    A = scaling_symbol(M, J, hs, DIRICHLET)
-    l = cyclic_generator_JT(J)
+    hs = np.array([L.point_of(HM, int(s)) for s in S.reshape(-1)], dtype=np.int64).reshape(len(gslots) * p, -1)
+    A = scaling_symbol(M, J, hs, DIRICHLET).reshape(len(gslots), p)
+    l = band_generator_JT(J)
     u = pattern_generator_J(J, l)
     adj = L.adjugate(M)
     D = L.det(M)
     sgn = 1 if D > 0 else -1
     # exact phase numerator of g^T M^{-1} u = sgn g^T adj(M) u / m
     au = [sum(adj[r][c] * u[c] for c in range(len(u))) for r in range(len(u))]
-    sym = np.zeros((p, m), dtype=np.complex128)
-    HN = L.hnf(L.transpose(exact_N(M, J)))
-    for gs in range(n):
-        g = L.point_of(HN, gs)
-        num = (sgn * sum(a * b for a, b in zip(g, au))) % m
+    HN = L.hnf(L.transpose(N))
+    b = np.zeros((len(gslots), p, p), dtype=np.complex128)
+    for i, gs in enumerate(gslots):
+        g = L.point_of(HN, int(gs))
+        num = (sgn * sum(x * y for x, y in zip(g, au))) % m
         e = np.exp(-2j * np.pi * num / m)
-        U = householder_completion(A[S[gs]] / np.sqrt(p))
-        for j in range(p):
-            sym[j, S[gs]] = np.sqrt(p) * U[j] * e ** j
+        U = householder_completion(A[i] / np.sqrt(p))
+        b[i] = np.sqrt(p) * U * (e ** np.arange(p))[:, None]
+    return S, b
+
+
+def dirichlet_p_symbols(M, J):
+    """Symbol system of a dilation J of prime determinant p = |det J| (this
+    project's reading of Section 5.3 step 4 for p bands):
+
+    * scaling symbol A(h) = sqrt(p w(N^{-T} h)), the periodised Dirichlet
+      weight of Section 6.2 (``scaling_symbol``), so sum_fibre |A|^2 = p;
+    * on the fibre h_t = g + t N^T l (t < p) of g in the box of H(N^T), l the
+      first unit vector outside J^T Z^d, with u_t = A(h_t) / sqrt(p) and U
+      the completion of u (``householder_completion``), the band symbols
+      b_j(h_t) = sqrt(p) U[j, t] e(g)^j, j < p, with
+      e(g) = exp(-2 pi i g^T N^{-1} z) for the centred generator z of P(J)
+      with l^T z = 1/p.
+
+    b_0 = A, and (b_j(h_t) / sqrt(p))_{j,t} is unitary on every fibre; for
+    p = 2 the system is the scaling / wavelet pair of Section 6.2.
+    Returns symbols [p, |det M|] on the box of H(M^T)."""
+    p = abs(L.det(J))
+    m = abs(L.det(M))
+    S, b = _band_system_at(M, J, range(m // p))
+    sym = np.zeros((p, m), dtype=np.complex128)
+    for i in range(len(S)):
+        sym[:, S[i]] = b[i]
     return sym
+
+
+def wavelet_bands_at(M, J, c_hat, gslots):
+    """The bands of ``wavelet_level_p`` at the slots gslots of the box of
+    H(N^T) only: d_j[g] = p^{-1/2} sum_t conj(b_j(h_t)) c(h_t) over the
+    fibre of each g.  c_hat [batch, |det M|] -> [p, batch, len(gslots)]."""
+    p = abs(L.det(J))
+    S, b = _band_system_at(M, J, gslots)
+    c = np.atleast_2d(np.asarray(c_hat, dtype=np.complex128))
+    return np.einsum("gjt,bgt->jbg", np.conj(b), c[:, S]) / np.sqrt(p)
 
 
 def wavelet_level_p(M, J, c_hat=None, parts=None, mode="decompose"):

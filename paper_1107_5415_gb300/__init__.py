@@ -21,6 +21,7 @@ import torch
 
 from . import _capi
 from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_BATCH_RADIX8, PFFT_C64, PFFT_C128, PFFT_FLAG_LAYOUT_SNF,
+                    pfft_batch_split_layout,
                     PFFT_FLAG_TC_SPLIT,
                     PFFT_MAP_INPUT_BOX,
                     PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_OUTPUT_SNF, PWT_DIRICHLET, PWT_DLVP,
@@ -35,7 +36,7 @@ from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_BATCH_RADIX8,
 __all__ = [
     "PatternFFT", "WaveletSplit", "PatternBatch", "pattern_fft", "pattern_ifft", "wavelet_decompose",
     "PFFT_BATCH_NO_GRAPH", "PFFT_BATCH_AUTOTUNE", "PFFT_BATCH_RADIX8", "PFFT_FLAG_TC_SPLIT", "PFFT_FLAG_LAYOUT_SNF", "PWT_FLAG_INPUT_SNF", "pfft_batch_create", "pfft_batch_info",
-    "pfft_batch_schedule", "pfft_batch_forward", "pfft_batch_destroy", "split_general", "merge_general",
+    "pfft_batch_schedule", "pfft_batch_split_layout", "pfft_batch_forward", "pfft_batch_destroy", "split_general", "merge_general",
     "pwt_split_general", "pwt_merge_general",
     "PfftError", "PFFT_C64", "PFFT_C128", "PWT_DIRICHLET", "PWT_DLVP",
     "PFFT_MAP_INPUT_BOX", "PFFT_MAP_OUTPUT_BOX", "PFFT_MAP_INPUT_SNF", "PFFT_MAP_OUTPUT_SNF",
@@ -241,8 +242,11 @@ class WaveletSplit:
 class PatternBatch:
     """Many patterns of uneven size, transformed (and split one level) together
     (wraps pfft_batch).  Signals are concatenated: pattern i owns elements
-    ``offsets[i] : offsets[i] + m[i]`` of the input and of ``c_hat``, and
-    ``offsets[i] // 2 : (offsets[i] + m[i]) // 2`` of the split parts."""
+    ``offsets[i] : offsets[i] + m[i]`` of the input and of ``c_hat``.  With
+    dilations J_i of determinant p_i, the scaling part of pattern i is
+    ``scaling[sc_off[i] : sc_off[i] + m[i] / p[i]]`` and its p_i - 1 band
+    parts are consecutive in ``wavelet`` from ``wv_off[i]`` (for p_i = 2 both
+    offsets are offsets[i] // 2)."""
 
     def __init__(self, Ms, Js=None, symbol: int = PWT_DIRICHLET, eta: float = 0.125, dtype=torch.complex64,
                  flags: int = 0):
@@ -252,6 +256,7 @@ class PatternBatch:
         self._h = pfft_batch_create(Ms, Js, symbol, eta, _dtype_code(dtype), flags)
         self.m, self.total = pfft_batch_info(self._h, self.n)
         self.offsets = np.concatenate([[0], np.cumsum(self.m)[:-1]]).astype(np.int64)
+        self.p, self.sc_off, self.wv_off, self.sc_total, self.wv_total = pfft_batch_split_layout(self._h, self.n)
 
     def schedule(self):
         """(row tile budget, column tile budget, order, largest power-of-two radix) chosen at creation."""
@@ -267,13 +272,12 @@ class PatternBatch:
         if not (self.has_split and split):
             pfft_batch_forward(self._h, x.data_ptr(), c_hat.data_ptr(), None, None, _stream(stream))
             return c_hat
-        half = self.total // 2
         if scaling is None:
-            scaling = torch.empty(half, dtype=self.dtype, device=dev)
+            scaling = torch.empty(self.sc_total, dtype=self.dtype, device=dev)
         if wavelet is None:
-            wavelet = torch.empty(half, dtype=self.dtype, device=dev)
-        _check_tensor(scaling, self.dtype, (half,), "scaling")
-        _check_tensor(wavelet, self.dtype, (half,), "wavelet")
+            wavelet = torch.empty(self.wv_total, dtype=self.dtype, device=dev)
+        _check_tensor(scaling, self.dtype, (self.sc_total,), "scaling")
+        _check_tensor(wavelet, self.dtype, (self.wv_total,), "wavelet")
         pfft_batch_forward(self._h, x.data_ptr(), c_hat.data_ptr(), scaling.data_ptr(), wavelet.data_ptr(),
                            _stream(stream))
         return c_hat, scaling, wavelet
@@ -290,28 +294,39 @@ class PatternBatch:
             pass
 
 
-def split_general(M, J, symbols: torch.Tensor, c_hat: torch.Tensor, stream=None) -> torch.Tensor:
-    """Section 5.3 step 4 for |det J| = p (cyclic G(J^T)) with caller symbols
-    [p, |det M|]: c_hat [batch, |det M|] -> parts [p, batch, |det M| / p]."""
-    p, m = symbols.shape
-    batch = c_hat.shape[0]
-    _check_tensor(symbols, c_hat.dtype, (p, m), "symbols")
+def _det_int(A) -> int:
+    A = np.asarray(A, dtype=np.int64)
+    return int(round(abs(np.linalg.det(A.astype(np.float64)))))
+
+
+def split_general(M, J, symbols, c_hat: torch.Tensor, stream=None) -> torch.Tensor:
+    """Section 5.3 step 4 for |det J| = p (cyclic G(J^T)): c_hat
+    [batch, |det M|] -> parts [p, batch, |det M| / p].  ``symbols``: the
+    caller's symbols [p, |det M|] (p <= 16), or None for the built-in
+    unitary band system (periodised Dirichlet scaling symbol and its
+    completion; any p)."""
+    batch, m = c_hat.shape
+    p = symbols.shape[0] if symbols is not None else _det_int(J)
     _check_tensor(c_hat, c_hat.dtype, (batch, m), "c_hat")
+    if symbols is not None:
+        _check_tensor(symbols, c_hat.dtype, (p, m), "symbols")
     out = torch.empty((p, batch, m // p), dtype=c_hat.dtype, device=c_hat.device)
-    pwt_split_general(M, J, batch, _dtype_code(c_hat.dtype), symbols.data_ptr(), c_hat.data_ptr(), out.data_ptr(),
-                      _stream(stream))
+    pwt_split_general(M, J, batch, _dtype_code(c_hat.dtype), symbols.data_ptr() if symbols is not None else 0,
+                      c_hat.data_ptr(), out.data_ptr(), _stream(stream))
     return out
 
 
-def merge_general(M, J, symbols: torch.Tensor, parts: torch.Tensor, stream=None) -> torch.Tensor:
-    """Adjoint of ``split_general`` (its inverse for unitary symbol systems)."""
+def merge_general(M, J, symbols, parts: torch.Tensor, stream=None) -> torch.Tensor:
+    """Adjoint of ``split_general`` (its inverse for unitary symbol systems,
+    the built-in one included: ``symbols`` None)."""
     p, batch, n = parts.shape
-    m = symbols.shape[1]
-    _check_tensor(symbols, parts.dtype, (p, m), "symbols")
+    m = p * n
     _check_tensor(parts, parts.dtype, (p, batch, n), "parts")
+    if symbols is not None:
+        _check_tensor(symbols, parts.dtype, (p, m), "symbols")
     out = torch.empty((batch, m), dtype=parts.dtype, device=parts.device)
-    pwt_merge_general(M, J, batch, _dtype_code(parts.dtype), symbols.data_ptr(), parts.data_ptr(), out.data_ptr(),
-                      _stream(stream))
+    pwt_merge_general(M, J, batch, _dtype_code(parts.dtype), symbols.data_ptr() if symbols is not None else 0,
+                      parts.data_ptr(), out.data_ptr(), _stream(stream))
     return out
 
 

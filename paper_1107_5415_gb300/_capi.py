@@ -78,6 +78,7 @@ _SIGS = {
     "pfft_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _i64p,
                                          _i64p, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_uint]),
     "pfft_batch_info": (ctypes.c_int, [_vp, _i64p, _i64p]),
+    "pfft_batch_split_layout": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), _i64p, _i64p, _i64p, _i64p]),
     "pfft_batch_schedule": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "pfft_batch_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -300,6 +301,17 @@ def pfft_batch_info(batch, n: int):
     total = ctypes.c_int64()
     _check(lib().pfft_batch_info(batch, mp, ctypes.byref(total)), "pfft_batch_info")
     return m, total.value
+
+
+def pfft_batch_split_layout(batch, n: int):
+    """(p [n], scaling offsets [n], wavelet offsets [n], scaling total, wavelet total)."""
+    p = (ctypes.c_int * n)()
+    so = np.zeros(n, dtype=np.int64)
+    wo = np.zeros(n, dtype=np.int64)
+    st, wt = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().pfft_batch_split_layout(batch, p, so.ctypes.data_as(_i64p), wo.ctypes.data_as(_i64p),
+                                         ctypes.byref(st), ctypes.byref(wt)), "pfft_batch_split_layout")
+    return np.array(list(p), dtype=np.int64), so, wo, int(st.value), int(wt.value)
 
 
 def pfft_batch_schedule(batch):

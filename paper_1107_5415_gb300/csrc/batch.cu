@@ -44,10 +44,14 @@ struct pfft_batch_s {
   std::vector<int64_t> m, off;
   int64_t total = 0;
   bool has_split = false;
-  std::vector<SplitItem> sitems;
+  std::vector<SplitItem> sitems;   // patterns whose dilation has |det J| = 2
+  std::vector<PrimeItem> pitems;   // |det J| = p > 2
+  std::vector<int> p;              // |det J_i| (0 without dilations)
+  std::vector<int64_t> sc_off, wv_off;
+  int64_t sc_total = 0, wv_total = 0;
   void* ws = nullptr;
   void* sched = nullptr;  // device: items and first-CTA tables of all launches
-  std::vector<Bucket> rows, cols, splits;
+  std::vector<Bucket> rows, cols, splits, primes;
   int row_budget = 8192, col_budget = 8192, order = 1, max2 = 16;
   std::vector<int> ident;  // patterns with m = 1 (the transform is a copy)
   cudaStream_t cap = nullptr;
@@ -206,6 +210,27 @@ pfft_status build_schedule(pfft_batch_s& B) {
     b.cta0_off = put(c0.data(), c0.size() * sizeof(int));
     sb.push_back(b);
   }
+  // prime split launch: one item per pattern with |det J| > 2, costliest first
+  std::vector<Bucket> pb;
+  if (!B.pitems.empty()) {
+    std::vector<int> porder;
+    for (int i = 0; i < int(B.pitems.size()); ++i) porder.push_back(i);
+    auto work = [&](int i) { return (long long)B.pitems[i].P.mN * B.pitems[i].P.nch; };
+    if (B.order == 1) std::stable_sort(porder.begin(), porder.end(), [&](int x, int y) { return work(x) > work(y); });
+    std::vector<PrimeItem> pi;
+    std::vector<int> c0(1, 0);
+    for (int i : porder) {
+      pi.push_back(B.pitems[i]);
+      c0.push_back(c0.back() + int((work(i) + kSplitThreads - 1) / kSplitThreads));
+    }
+    Bucket b;
+    b.n = int(pi.size());
+    b.nctas = c0.back();
+    b.threads = kSplitThreads;
+    b.items_off = put(pi.data(), pi.size() * sizeof(PrimeItem));
+    b.cta0_off = put(c0.data(), c0.size() * sizeof(int));
+    pb.push_back(b);
+  }
   void* dev = nullptr;
   if (!host.empty()) {
     if (int e = device_alloc(&dev, host.size())) return pfft_status(e);
@@ -219,6 +244,7 @@ pfft_status build_schedule(pfft_batch_s& B) {
   B.rows = rb;
   B.cols = cb;
   B.splits = sb;
+  B.primes = pb;
   if (B.exec) {  // the graph refers to the old schedule
     cudaGraphExecDestroy(B.exec);
     B.exec = nullptr;
@@ -266,6 +292,13 @@ pfft_status enqueue(pfft_batch_s& B, const void* in, void* chat, void* sc, void*
     if (launch_grouped_split(reinterpret_cast<const SplitItem*>(sched + b.items_off),
                              reinterpret_cast<const int*>(sched + b.cta0_off), b.n, b.nctas, chat, sc, wv, B.dtype,
                              s) != 0)
+      return PFFT_ERR_CUDA;
+  }
+  if (sc && wv && !B.primes.empty()) {
+    const Bucket& b = B.primes[0];
+    if (launch_grouped_prime_split(reinterpret_cast<const PrimeItem*>(sched + b.items_off),
+                                   reinterpret_cast<const int*>(sched + b.cta0_off), b.n, b.nctas, chat, sc, wv,
+                                   B.dtype, s) != 0)
       return PFFT_ERR_CUDA;
   }
   return PFFT_OK;
@@ -334,8 +367,8 @@ pfft_status autotune(pfft_batch_s& B) {
   if (int e = device_alloc(&in, size_t(B.total) * eb)) return fail(pfft_status(e));
   if (int e = device_alloc(&chat, size_t(B.total) * eb)) return fail(pfft_status(e));
   if (B.has_split) {
-    if (int e = device_alloc(&sc, size_t(B.total / 2) * eb)) return fail(pfft_status(e));
-    if (int e = device_alloc(&wv, size_t(B.total / 2) * eb)) return fail(pfft_status(e));
+    if (int e = device_alloc(&sc, size_t(std::max<int64_t>(B.sc_total, 1)) * eb)) return fail(pfft_status(e));
+    if (int e = device_alloc(&wv, size_t(std::max<int64_t>(B.wv_total, 1)) * eb)) return fail(pfft_status(e));
   }
   if (cudaMemset(in, 0, size_t(B.total) * eb) != cudaSuccess) return fail(PFFT_ERR_CUDA);
   const int budgets[] = {2048, 4096, 8192, 16384};
@@ -426,16 +459,50 @@ extern "C" pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, c
     if (P->D == 0) B->ident.push_back(i);
     if (!P->pen.empty()) need_ws = true;
     if (J) {
-      SplitItem it;
-      std::memset(&it, 0, sizeof(it));
-      st = describe_split_level(d[i], M + mo, J + mo, symbol, eta, &it.L);
-      if (st != PFFT_OK) return fail(st);
-      void* tab = nullptr;  // phase tables in the arena, as single plans have them
-      if (int e = B->arena.alloc(&tab, split_table_elems(it.L) * ebytes(dtype))) return fail(pfft_status(e));
-      if (launch_split_tables(it.L, tab, dtype) != 0) return fail(PFFT_ERR_CUDA);
-      it.in_off = B->off[i];
-      it.out_off = B->off[i] / 2;
-      B->sitems.push_back(it);
+      i64 pdet = 0;
+      try {
+        IMat Jm(d[i]);
+        for (int k = 0; k < d[i] * d[i]; ++k) Jm.a[k] = J[mo + k];
+        pdet = determinant(Jm);
+      } catch (const LatticeError& e) {
+        return fail(pfft_status(e.code));
+      }
+      if (pdet < 0) pdet = -pdet;
+      if (pdet < 2 || pdet > (i64(1) << 20) || P->m % pdet != 0) return fail(pdet == 0 ? PFFT_ERR_SINGULAR
+                                                                                     : PFFT_ERR_NOT_INTEGRAL);
+      const int64_t n_i = P->m / pdet;
+      if (pdet == 2) {
+        SplitItem it;
+        std::memset(&it, 0, sizeof(it));
+        st = describe_split_level(d[i], M + mo, J + mo, symbol, eta, &it.L);
+        if (st != PFFT_OK) return fail(st);
+        void* tab = nullptr;  // phase tables in the arena, as single plans have them
+        if (int e = B->arena.alloc(&tab, split_table_elems(it.L) * ebytes(dtype))) return fail(pfft_status(e));
+        if (launch_split_tables(it.L, tab, dtype) != 0) return fail(PFFT_ERR_CUDA);
+        it.in_off = B->off[i];
+        it.sc_off = B->sc_total;
+        it.wv_off = B->wv_total;
+        B->sitems.push_back(it);
+      } else {
+        if (symbol != PWT_DIRICHLET) return fail(PFFT_ERR_UNSUPPORTED);  // built-in bands: Dirichlet only
+        PrimeItem it;
+        std::memset(&it, 0, sizeof(it));
+        try {
+          st = describe_prime_level(d[i], M + mo, J + mo, &it.P);
+        } catch (const LatticeError& e) {
+          st = pfft_status(e.code);
+        }
+        if (st != PFFT_OK) return fail(st);
+        it.in_off = B->off[i];
+        it.sc_off = B->sc_total;
+        it.wv_off = B->wv_total;
+        B->pitems.push_back(it);
+      }
+      B->p.push_back(int(pdet));
+      B->sc_off.push_back(B->sc_total);
+      B->wv_off.push_back(B->wv_total);
+      B->sc_total += n_i;
+      B->wv_total += (pdet - 1) * n_i;
     }
     mo += size_t(d[i]) * d[i];
   }
@@ -465,6 +532,20 @@ extern "C" pfft_status pfft_batch_info(pfft_batch b, int64_t* m, int64_t* total)
   if (m)
     for (int i = 0; i < b->n; ++i) m[i] = b->m[i];
   if (total) *total = b->total;
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pfft_batch_split_layout(pfft_batch b, int* p, int64_t* scaling_off, int64_t* wavelet_off,
+                                               int64_t* scaling_total, int64_t* wavelet_total) {
+  if (!b) return PFFT_ERR_ARG;
+  for (int i = 0; i < b->n; ++i) {
+    const bool has = b->has_split;
+    if (p) p[i] = has ? b->p[i] : 0;
+    if (scaling_off) scaling_off[i] = has ? b->sc_off[i] : 0;
+    if (wavelet_off) wavelet_off[i] = has ? b->wv_off[i] : 0;
+  }
+  if (scaling_total) *scaling_total = b->sc_total;
+  if (wavelet_total) *wavelet_total = b->wv_total;
   return PFFT_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "fft_plan.hpp"
+#include "split_prime.cuh"
 #include "wavelet_kernels.cuh"
 
 namespace pfft {
@@ -25,11 +26,20 @@ struct GroupArgs {
   const void* base[3];  // 0: the caller's input, 1: the batch workspace, 2: the caller's output
 };
 
-// One split level of one pattern; offsets in elements into the concatenated
-// c_hat (in_off) and split parts (out_off).
+// One split level of one pattern with |det J| = 2; offsets in elements into
+// the concatenated c_hat (in_off), scaling parts (sc_off) and wavelet parts
+// (wv_off).
 struct alignas(16) SplitItem {
   LevelDesc L;
-  long long in_off, out_off;
+  long long in_off, sc_off, wv_off;
+};
+
+// One split level of one pattern with |det J| = p > 2 (built-in band
+// system, split_prime.cuh): band 0 at scaling + sc_off, band j >= 1 at
+// wavelet + wv_off + (j - 1) |det N|.
+struct alignas(16) PrimeItem {
+  PrimeDesc P;
+  long long in_off, sc_off, wv_off;
 };
 
 // Raise the dynamic shared-memory limit of the grouped kernels (once per
@@ -39,5 +49,10 @@ int launch_grouped_pass(const GroupArgs& g, int cols, int dtype, int nctas, int 
                         cudaStream_t s);
 int launch_grouped_split(const SplitItem* items, const int* cta0, int n, int nctas, const void* chat, void* sc,
                          void* wv, int dtype, cudaStream_t s);
+// The split levels of the patterns with |det J| > 2: items[k]'s work items
+// (fibre, chunk of kPrimeChunk bands) start at CTA cta0[k], kSplitThreads
+// items per CTA.
+int launch_grouped_prime_split(const PrimeItem* items, const int* cta0, int n, int nctas, const void* chat,
+                               void* sc, void* wv, int dtype, cudaStream_t s);
 
 }  // namespace pfft

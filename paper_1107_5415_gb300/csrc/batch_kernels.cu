@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(kSplitThreads) grouped_split_kernel(const Spli
   __syncthreads();
   const int g0 = (blockIdx.x - __ldg(cta0 + k)) * (kSplitThreads * kSplitPerThread) + threadIdx.x;
   const C* cin = chat + it.in_off;
-  C* d1 = sc + it.out_off;
-  C* d2 = wv + it.out_off;
+  C* d1 = sc + it.sc_off;
+  C* d2 = wv + it.wv_off;
 #pragma unroll
   for (int f = 0; f < kSplitPerThread; ++f) {
     const int gs = g0 + f * kSplitThreads;
@@ -81,6 +81,23 @@ __global__ void __launch_bounds__(kSplitThreads) grouped_split_kernel(const Spli
     else
       split_fibre<C, 0, true, false>(it.L, gs, 1, cin, nullptr, nullptr, nullptr, d1, d2);
   }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kSplitThreads) grouped_prime_kernel(const PrimeItem* __restrict__ items,
+                                                                      const int* __restrict__ cta0, int n,
+                                                                      const C* __restrict__ chat,
+                                                                      C* __restrict__ sc, C* __restrict__ wv) {
+  __shared__ PrimeItem it;
+  const int k = find_item(cta0, n, blockIdx.x);
+  copy_to_smem(&it, items + k);
+  __syncthreads();
+  const long long w = (long long)(blockIdx.x - __ldg(cta0 + k)) * kSplitThreads + threadIdx.x;
+  const long long mN = it.P.mN;
+  if (w >= mN * it.P.nch) return;
+  const int ch = int(w / mN), gs = int(w - ch * mN);
+  prime_split_item<C, 0>(it.P, gs, ch * kPrimeChunk, chat + it.in_off, nullptr, nullptr, nullptr,
+                         sc + it.sc_off + gs, wv + it.wv_off + gs, mN);
 }
 
 namespace {
@@ -135,4 +152,18 @@ int launch_grouped_split(const SplitItem* items, const int* cta0, int n, int nct
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+}  // namespace pfft
+
+namespace pfft {
+int launch_grouped_prime_split(const PrimeItem* items, const int* cta0, int n, int nctas, const void* chat,
+                               void* sc, void* wv, int dtype, cudaStream_t s) {
+  if (nctas <= 0) return 0;
+  if (dtype == 0)
+    grouped_prime_kernel<float2><<<nctas, kSplitThreads, 0, s>>>(
+        items, cta0, n, static_cast<const float2*>(chat), static_cast<float2*>(sc), static_cast<float2*>(wv));
+  else
+    grouped_prime_kernel<double2><<<nctas, kSplitThreads, 0, s>>>(
+        items, cta0, n, static_cast<const double2*>(chat), static_cast<double2*>(sc), static_cast<double2*>(wv));
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 }  // namespace pfft

@@ -29,7 +29,7 @@ WORKLOADS = {
     "batched_2d": dict(M=M_BATCHED_2D, batch=8, seed=1),
     "autograd_3d": dict(M=M_AUTOGRAD_3D, batch=4, seed=2),
     "wavelet_2d": dict(M=M_WAVELET_2D, batch=16, seed=3, levels=12),
-    "uneven_mix": dict(n_patterns=4096, seed=4, even_det=True),
+    "uneven_mix": dict(n_patterns=4096, seed=4, even_det=False),
     "directional": dict(M=M_DIRECTIONAL, batch=16, seed=5),
     "table1": dict(n=2048, batch=8, seed=6),
 }

@@ -166,22 +166,82 @@ def test_batch_errors():
         B.forward(x.cpu())
 
 
+def _bands_of(B, i, sc, wv):
+    """[p, n] bands of pattern i of a batch (band 0: the scaling part)."""
+    p, n = int(B.p[i]), int(B.m[i]) // int(B.p[i])
+    s0, w0 = int(B.sc_off[i]), int(B.wv_off[i])
+    return np.concatenate([sc[None, s0:s0 + n], wv[w0:w0 + (p - 1) * n].reshape(p - 1, n)])
+
+
+def _bands_ref_at(M, J, c, gslots):
+    """Oracle bands at the slots gslots of the box of H(N^T) (prime |det J|):
+    the oracle's transform on the p members of each fibre, then its p-band
+    split of the coefficient vector holding only those values."""
+    members = oracle.band_fibre_slots(M, J, gslots)
+    slots = np.unique(members.reshape(-1))
+    sparse = np.zeros((1, abs(L.det(M))), np.complex128)
+    sparse[0, slots] = oracle.pattern_fft(M, c[None, :], out_slots=slots)[0]
+    return oracle.wavelet_bands_at(M, J, sparse, gslots)[:, 0]
+
+
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_small_mix_mixed_determinants_full(dtype):
+    """Patterns of even and odd determinant, each split by its mix dilation
+    (determinant 2, or the smallest odd prime of det M: the built-in band
+    system), every output of every pattern against the oracle."""
+    Ms = SI.uneven_mix(40, seed=90, max_det=4096, lo=2, hi=40, even_det=False) + \
+        [[[37, 5], [0, 74]], [[3, 1], [0, 9]], [[7, 2, 1], [0, 5, 3], [0, 0, 3]], [[31, 7], [0, 31]]]
+    Js = [SI.mix_dilation(M) for M in Ms]
+    B = pf.PatternBatch(Ms, Js, pf.PWT_DIRICHLET, dtype=dtype)
+    assert sorted(set(int(p) for p in B.p)) != [2]
+    c128 = dtype == torch.complex128
+    tol = 1e-12 if c128 else 1e-5
+    x = SI.complex_normal_flat(B.total, 91).astype(np.complex128 if c128 else np.complex64)
+    chat, sc, wv = (_np(t) for t in B.forward(torch.from_numpy(x).cuda()))
+    assert len(sc) == B.sc_total and len(wv) == B.wv_total
+    for i, (M, J) in enumerate(zip(Ms, Js)):
+        o, m = int(B.offsets[i]), int(B.m[i])
+        ref = oracle.pattern_fft(M, x[None, o:o + m])
+        assert rel_l2(chat[o:o + m], ref[0]) <= tol, (i, M)
+        bands = _bands_of(B, i, sc, wv)
+        if B.p[i] == 2:
+            d1, d2 = oracle.wavelet_level(M, J, pf.PWT_DIRICHLET, c_hat=ref)
+            want = np.stack([d1[0], d2[0]])
+        else:
+            want = oracle.wavelet_level_p(M, J, c_hat=ref)[:, 0]
+        assert rel_l2(bands.reshape(1, -1), want.reshape(1, -1)) <= tol, (i, M, int(B.p[i]))
+
+
+def test_odd_determinant_needs_the_dirichlet_bands():
+    with pytest.raises(pf.PfftError) as e:
+        pf.PatternBatch([[[9, 0], [0, 3]]], [[[3, 0], [0, 1]]], pf.PWT_DLVP, 0.125)
+    assert e.value.status == 5
+
+
 def test_uneven_mix_full_size_sampled():
     """The uneven serving-style mix in the benchmark's configuration
-    (autotuned schedule, graph replay, Dirichlet symbol)."""
+    (4096 patterns drawn as the rules state, odd determinants included;
+    each split by its mix dilation; autotuned schedule, graph replay,
+    Dirichlet symbol)."""
     w = SI.WORKLOADS["uneven_mix"]
     Ms = SI.uneven_mix(w["n_patterns"], seed=w["seed"], even_det=w["even_det"])
-    Js = [SI.parity_dilation(M) for M in Ms]
+    Js = [SI.mix_dilation(M) for M in Ms]
     B = pf.PatternBatch(Ms, Js, pf.PWT_DIRICHLET, flags=pf.PFFT_BATCH_AUTOTUNE)
+    assert (B.p % 2 == 1).sum() > 0
     x = SI.complex_normal_flat(B.total, w["seed"])
     chat, sc, wv = (_np(t) for t in B.forward(torch.from_numpy(x).cuda()))
     off, ms = B.offsets, B.m
-    # Parseval and the Dirichlet split's norm identity, every pattern
+    # Parseval and the norm identity of the unitary split, every pattern
     e_x = np.add.reduceat(np.abs(x.astype(np.complex128)) ** 2, off)
     e_c = np.add.reduceat(np.abs(chat.astype(np.complex128)) ** 2, off)
-    e_s = np.add.reduceat(np.abs(sc.astype(np.complex128)) ** 2 + np.abs(wv.astype(np.complex128)) ** 2, off // 2)
+    e_s = np.add.reduceat(np.abs(sc.astype(np.complex128)) ** 2, B.sc_off)
+    e_w = np.zeros(len(Ms))
+    a_w = np.abs(wv.astype(np.complex128)) ** 2
+    for i in range(len(Ms)):
+        n = int(ms[i]) // int(B.p[i])
+        e_w[i] = a_w[int(B.wv_off[i]):int(B.wv_off[i]) + (int(B.p[i]) - 1) * n].sum()
     assert np.allclose(e_c, e_x, rtol=1e-5)
-    assert np.allclose(e_s, e_c, rtol=1e-5)
+    assert np.allclose(e_s + e_w, e_c, rtol=1e-5)
     rng = np.random.default_rng(SI.SAMPLE_SEED)
     worst = 0.0
     for i, M in enumerate(Ms):
@@ -189,8 +249,14 @@ def test_uneven_mix_full_size_sampled():
         slots = np.sort(rng.choice(m, 8, replace=False))
         ref = oracle.pattern_fft(M, x[None, o:o + m], out_slots=slots)[0]
         worst = max(worst, rel_l2(chat[o + slots], ref))
-        if i % 8 == 0:
-            g = np.sort(rng.choice(m // 2, 2, replace=False))
-            d1, d2 = _split_ref_at(M, Js[i], x[o:o + m], g, pf.PWT_DIRICHLET)
-            worst = max(worst, rel_l2(sc[o // 2 + g], d1), rel_l2(wv[o // 2 + g], d2))
+        p = int(B.p[i])
+        if i % 8 == 0 or (p > 2 and i % 2 == 0):
+            g = np.sort(rng.choice(m // p, 2, replace=False))
+            bands = _bands_of(B, i, sc, wv)[:, g]
+            if p == 2:
+                d1, d2 = _split_ref_at(M, Js[i], x[o:o + m], g, pf.PWT_DIRICHLET)
+                want = np.stack([d1, d2])
+            else:
+                want = _bands_ref_at(M, Js[i], x[o:o + m], g)
+            worst = max(worst, rel_l2(bands.reshape(1, -1), want.reshape(1, -1)))
     assert worst <= 1e-5, worst

@@ -73,3 +73,42 @@ def test_general_split_errors():
         pf.split_general([[17, 0], [0, 2]], [[17, 0], [0, 1]], big, torch.zeros(1, 34, dtype=torch.complex64,
                                                                                device="cuda"))
     assert e.value.status == 5
+
+
+# Built-in band system (symbols NULL): dilations of prime determinant p
+# (the harness's prime dilation for the p dividing det M), against the
+# oracle's Householder-completed Dirichlet system.
+BUILTIN = [([[9, 0], [0, 9]], [[3, 0], [0, 1]]),
+           ([[9, 6], [9, 15]], [[1, 0], [-2, 3]]),
+           ([[15, 5], [0, 10]], [[1, 0], [0, 5]]),
+           ([[6, 1, 2], [0, 7, 3], [0, 0, 14]], [[1, 0, 0], [0, 1, 0], [0, 0, 7]]),
+           ([[31, 7], [0, 62]], SI.prime_dilation([[31, 7], [0, 62]], 31)),
+           ([[127, 3], [0, 254]], SI.prime_dilation([[127, 3], [0, 254]], 127)),
+           ([[8, 8], [-8, 8]], SI.J_DIAG_A)]
+
+
+@pytest.mark.parametrize("case", range(len(BUILTIN)))
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_builtin_band_system_vs_oracle(case, dtype):
+    M, J = BUILTIN[case]
+    m, p = abs(L.det(M)), abs(L.det(J))
+    c = SI.complex_normal(2, m, 70 + case, dtype=np.complex128)
+    tol = TOL["c64" if dtype == torch.complex64 else "c128"]
+    parts = pf.split_general(M, J, None, _gpu(c, dtype)).cpu().numpy()
+    ref = oracle.wavelet_level_p(M, J, c_hat=c)
+    for j in range(p):
+        assert rel_l2(parts[j], ref[j]) <= tol or np.linalg.norm(ref[j]) < 1e-12 * np.linalg.norm(c), j
+    assert rel_l2(parts.transpose(1, 0, 2).reshape(2, -1), ref.transpose(1, 0, 2).reshape(2, -1)) <= tol
+    back = pf.merge_general(M, J, None, _gpu(ref, dtype)).cpu().numpy()
+    assert rel_l2(back, c) <= tol
+
+
+def test_builtin_band_system_p2_equals_the_dirichlet_split():
+    """For p = 2 the built-in system is the split of pwt_decompose (Dirichlet)."""
+    M, J = [[64, 64], [-64, 64]], SI.J_DIAG_A
+    c = _gpu(SI.complex_normal(3, 8192, 77), torch.complex64)
+    parts = pf.split_general(M, J, None, c)
+    plan = pf.WaveletSplit(M, [J], pf.PWT_DIRICHLET, 0.125, 3)
+    s, w = plan.decompose(c)
+    assert rel_l2(parts[0].cpu().numpy(), s.cpu().numpy()) <= 1e-6
+    assert rel_l2(parts[1].cpu().numpy(), w[0].cpu().numpy()) <= 1e-6

@@ -191,6 +191,43 @@ def test_parity_dilation_divides_pattern(seed):
         oracle.exact_N(M, J)  # raises unless J^{-1} M is integral
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_prime_dilation_divides_pattern(seed):
+    """The dilation of any prime p dividing det M: |det J| = p and J^{-1} M
+    integral; primes not dividing det M are refused."""
+    rng = np.random.default_rng(100 + seed)
+    for _ in range(30):
+        d = int(rng.integers(1, 5))
+        M = SI.random_regular_matrix(rng, d, 9, 1 << 16)
+        D = abs(L.det(M))
+        for p in (2, 3, 5, 7, 11, 13):
+            if D % p:
+                with pytest.raises(ValueError):
+                    SI.prime_dilation(M, p)
+                continue
+            J = SI.prime_dilation(M, p)
+            assert abs(L.det(J)) == p
+            oracle.exact_N(M, J)
+
+
+def test_mix_dilations_of_the_uneven_mix():
+    """Every pattern of the uneven mix (drawn without the even filter) gets a
+    dilation of determinant 2 or of the smallest odd prime of its
+    determinant, with J^{-1} M integral."""
+    w = SI.WORKLOADS["uneven_mix"]
+    Ms = SI.uneven_mix(w["n_patterns"], seed=w["seed"], even_det=w["even_det"])
+    odd = 0
+    for M in Ms:
+        D = abs(L.det(M))
+        J = SI.mix_dilation(M)
+        p = abs(L.det(J))
+        assert p == SI.smallest_prime_factor(D)
+        odd += p > 2
+        if p > 2:
+            assert D % 2 == 1
+    assert odd > 0.15 * len(Ms)
+
+
 def test_plan_argument_errors():
     with pytest.raises(pf.PfftError) as e:
         pf.pfft_plan_create([[2, 1], [4, 2]], 1)

@@ -674,3 +674,14 @@ def test_pattern_generator_pairs_to_one_over_p(M, J):
     z = L.matvec(L.inverse(J), u)
     assert all(Fraction(-1, 2) <= x < Fraction(1, 2) for x in z)
     assert (sum(Fraction(a) * b for a, b in zip(l, z)) - Fraction(1, p)).denominator == 1
+
+
+@pytest.mark.parametrize("M,J", P_CASES[:4])
+def test_bands_at_sampled_fibres_equal_the_full_split(M, J):
+    """wavelet_bands_at (the sampled form the large-size GPU checks use) gives
+    the full split's values at the chosen fibres."""
+    m, p = abs(L.det(M)), abs(L.det(J))
+    c = _rand_c(m, 2, 12)
+    full = oracle.wavelet_level_p(M, J, c_hat=c)
+    g = np.array([0, 1, m // p - 1])
+    assert np.allclose(oracle.wavelet_bands_at(M, J, c, g), full[:, :, g], atol=1e-13)
