@@ -60,9 +60,10 @@ def measured_peaks():
 
 # sources that define each measured kernel and its launch configuration
 KERNEL_SOURCES = {
-    "row_pass": ["fft_tma.cuh", "fft_tma.cu", "fft_tma_ct.cuh", "fft_fast_ct.cuh", "fft_fast.cuh",
-                 "device_common.cuh"],
-    "col_pass": ["fft_fast.cuh", "fft_fast_f32.cu", "fft_fast_ct.cuh", "fft_fast_ct.cu", "device_common.cuh"],
+    "row_pass": ["fft_row_pipe.cuh", "fft_tma.cu", "fft_tma.cuh", "fft_fast_ct.cuh", "fft_fast.cuh",
+                 "device_common.cuh", "fft_plan.hpp"],
+    "col_pass": ["fft_col_pipe.cuh", "fft_fast_ct.cu", "fft_fast_ct.cuh", "fft_fast.cuh", "device_common.cuh",
+                 "fft_plan.hpp"],
 }
 
 

@@ -103,6 +103,7 @@ struct pwt_plan_s {
   std::vector<i64> sizes;     // |det M_l|
   std::vector<IMat> boxes;    // H(M_l^T)
   std::vector<LevelDesc> lv;  // device descriptors
+  LevelDesc* dlv = nullptr;   // the same in device memory (fused launches)
   void* tables = nullptr;     // phase tables of all levels
   void* ws[2] = {nullptr, nullptr};
   Profiler prof;
@@ -113,6 +114,7 @@ static size_t cbytes(int dtype) { return dtype == PFFT_C64 ? 8 : 16; }
 static void release(pwt_plan_s* P) {
   if (!P) return;
   if (P->tables) cudaFree(P->tables);
+  if (P->dlv) cudaFree(P->dlv);
   for (auto p : P->ws)
     if (p) cudaFree(p);
   delete P;
@@ -376,6 +378,9 @@ static pfft_status plan_device(pwt_plan_s& P) {
       phase_table_kernel<double2><<<grd, blk>>>((double2*)L.tab_lo, (double2*)L.tab_hi, L.q, nhi);
     if (cudaGetLastError() != cudaSuccess) return PFFT_ERR_CUDA;
   }
+  if (int e_ = device_alloc((void**)&P.dlv, sizeof(LevelDesc) * P.lv.size())) return pfft_status(e_);
+  if (cudaMemcpy(P.dlv, P.lv.data(), sizeof(LevelDesc) * P.lv.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return PFFT_ERR_CUDA;
   if (P.levels > 1) {
     const size_t half = size_t(P.sizes[0] / 2) * P.batch * cb;
     for (int i = 0; i < 2; ++i)
@@ -443,6 +448,50 @@ static int run_level(pwt_plan_s* P, int l, int mode, const void* cin, void* cout
   return rc;
 }
 
+// Levels l, l + 1, ... that one fused launch takes (fused_split_kernel):
+// complex64, int32 index paths, the first level's input in box order; 1 when
+// the level runs alone.
+static int fuse_count(const pwt_plan_s* P, int l) {
+  if (P->dtype != PFFT_C64 || P->lv[l].snf_D) return 1;
+  int F = 0;
+  while (F < kFuseMax && l + F < P->levels && P->lv[l + F].small) ++F;
+  return F < 2 ? 1 : F;
+}
+
+template <int F>
+static int launch_fused_t(pwt_plan_s* P, int l, const void* cin, void* sout, void* const* wavelets,
+                          cudaStream_t s) {
+  constexpr int smem = fused_smem_bytes<float2, F>();
+  static const bool ok = cudaFuncSetAttribute(reinterpret_cast<const void*>(fused_split_kernel<float2, F>),
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+  if (!ok) return -1;
+  // fibres of the last level over CTAs of kFuseThreads threads, about
+  // kFuseWaves resident waves; the signals split into chunks only when the
+  // fibres are too few
+  const long long mN = P->lv[l + F - 1].mN, cap = 152LL * kFuseWaves;
+  long long x = (mN + kFuseThreads - 1) / kFuseThreads;
+  if (x > cap) x = cap;
+  long long y = (cap + x - 1) / x;
+  if (y > P->batch) y = P->batch;
+  const int chunk = int((P->batch + y - 1) / y);
+  const unsigned gy = unsigned((P->batch + chunk - 1) / chunk);
+  float2* w[3] = {nullptr, nullptr, nullptr};
+  for (int k = 0; k < F; ++k) w[k] = static_cast<float2*>(wavelets[l + k]);
+  fused_split_kernel<float2, F><<<dim3(unsigned(x), gy), kFuseThreads, smem, s>>>(
+      P->dlv + l, int(P->batch), chunk, static_cast<const float2*>(cin), static_cast<float2*>(sout), w[0], w[1],
+      w[2]);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+static int launch_fused(pwt_plan_s* P, int l, int F, const void* cin, void* sout, void* const* wavelets,
+                        cudaStream_t s) {
+  P->prof.begin(0, s);
+  const int rc = F == 3 ? launch_fused_t<3>(P, l, cin, sout, wavelets, s)
+                        : launch_fused_t<2>(P, l, cin, sout, wavelets, s);
+  P->prof.end(0, s);
+  return rc;
+}
+
 extern "C" pfft_status pwt_decompose(pwt_plan p, const void* c_hat, void* scaling, void* const* wavelets,
                                      void* stream) {
   if (!p || !c_hat || !scaling || !wavelets) return PFFT_ERR_ARG;
@@ -450,10 +499,15 @@ extern "C" pfft_status pwt_decompose(pwt_plan p, const void* c_hat, void* scalin
     if (!wavelets[l]) return PFFT_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const void* cur = c_hat;
-  for (int l = 0; l < p->levels; ++l) {
-    void* d1 = (l == p->levels - 1) ? scaling : p->ws[l & 1];
-    if (run_level(p, l, 0, cur, nullptr, nullptr, nullptr, d1, wavelets[l], s) != 0) return PFFT_ERR_CUDA;
+  int g = 0;  // launches so far: their scaling parts alternate between the two workspaces
+  for (int l = 0; l < p->levels; ++g) {
+    const int F = fuse_count(p, l);
+    void* d1 = (l + F == p->levels) ? scaling : p->ws[g & 1];
+    const int rc = F > 1 ? launch_fused(p, l, F, cur, d1, wavelets, s)
+                         : run_level(p, l, 0, cur, nullptr, nullptr, nullptr, d1, wavelets[l], s);
+    if (rc != 0) return PFFT_ERR_CUDA;
     cur = d1;
+    l += F;
   }
   return PFFT_OK;
 }

@@ -235,6 +235,168 @@ __global__ void __launch_bounds__(256) split_kernel(LevelDesc L, int batch, int 
                                      MODE == 0 ? d1out + oN : nullptr, MODE == 0 ? d2out + oN : nullptr);
 }
 
+// ---- Several levels in one launch (the repetition of steps 2-4 at the end
+// of Section 5.3).  After F levels, a fibre g of G(N_F^T) (the last level's
+// output) draws on 2^F coefficients of the first level's input: its two
+// members are fibres of level F - 1, theirs of level F - 2, and so on.  One
+// thread takes g, reads those 2^F inputs once per signal, runs the 2^F - 1
+// butterflies of the tree level by level and writes every wavelet part once
+// and the last scaling part; the scaling parts of the inner levels never
+// leave registers.  The symbols depend on the fibres only: each thread
+// evaluates them once per g (top-down, so that only the box points of the
+// current level are live) into its column of shared-memory tables and
+// applies them to every signal of its chunk, two signals at a time so that
+// the loads of both are in flight together.
+constexpr int kFuseThreads = 128;
+constexpr int kFuseMax = 3;   // levels per launch (4 needs more registers than pays off)
+constexpr int kFuseWaves = 8; // resident waves of CTAs for the fibres
+
+// Dynamic shared memory of fused_split_kernel<C, F>: per thread and fibre of
+// the tree (2^F - 1) the symbols (A(h0), A(h1), conjugate phase) and the
+// output slot, per member of the first level (2^F) the input slot.
+template <typename C, int F>
+__host__ __device__ constexpr int fused_smem_bytes() {
+  return kFuseThreads * (((1 << F) - 1) * (4 * int(sizeof(decltype(C::x))) + 4) + (1 << F) * 4);
+}
+
+// F levels of the analysis (mode 0) starting at the level whose descriptor is
+// lvg[0]: inputs cin (the first level's coefficients), wavelet parts of level
+// k at w_k, the last scaling part at sout; signals [y chunk, (y + 1) chunk).
+// Every level of the group has the int32 index path (`small`).
+template <typename C, int F>
+__global__ void __launch_bounds__(kFuseThreads, 4)
+    fused_split_kernel(const LevelDesc* __restrict__ lvg, int batch, int chunk, const C* __restrict__ cin,
+                       C* __restrict__ sout, C* __restrict__ w0, C* __restrict__ w1, C* __restrict__ w2) {
+  using Rl = decltype(C::x);
+  constexpr int NT = kFuseThreads;
+  constexpr int NL = 1 << (F - 1);   // fibres of the first level per thread
+  constexpr int FIB = (1 << F) - 1;  // fibres of the tree
+  constexpr int SG = 2;              // signals per iteration
+  __shared__ LevelDesc lv[F];
+  extern __shared__ __align__(16) unsigned char fsm[];
+  // per-thread tables, thread index fastest: symbols [FIB][4][NT] (A0, A1,
+  // phase), output slots [FIB][NT], input slots [2^F][NT]
+  Rl* sym = reinterpret_cast<Rl*>(fsm);
+  int* osl = reinterpret_cast<int*>(fsm + size_t(FIB) * NT * 4 * sizeof(Rl));
+  int* isl = osl + FIB * NT;
+  static_assert(sizeof(LevelDesc) % 4 == 0, "level descriptors are copied as 32-bit words");
+  for (int i = threadIdx.x; i < int(F * sizeof(LevelDesc) / 4); i += blockDim.x)
+    reinterpret_cast<int*>(lv)[i] = __ldg(reinterpret_cast<const int*>(lvg) + i);
+  __syncthreads();
+  const int b0 = blockIdx.y * chunk;
+  const int nb = min(chunk, batch - b0);
+  if (nb <= 0) return;
+  const LevelDesc& Lt = lv[F - 1];
+  C* const wout[3] = {w0, w1, w2};
+  const int tid = threadIdx.x;
+  // fibre i of level k has the flat index 2^(F-1-k) - 1 + i in the tables
+  for (int gs = blockIdx.x * NT + tid; gs < Lt.mN; gs += gridDim.x * NT) {
+    int cur[NL][4];
+    {
+      int s = gs;
+#pragma unroll
+      for (int r = 3; r >= 0; --r) {
+        cur[0][r] = 0;
+        if (r < Lt.d) {
+          const int qd = Lt.divHN[r].div(s);
+          cur[0][r] = s - qd * Lt.HNext[r];
+          s = qd;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = F - 1; k >= 0; --k) {
+      const LevelDesc& L = lv[k];
+#pragma unroll
+      for (int i = 0; i < (1 << (F - 1 - k)); ++i) {
+        const int f = (1 << (F - 1 - k)) - 1 + i;
+        const Rl w = fibre_weight<Rl, true>(L, cur[i]);
+        Rl a0, a1;
+        if (L.symbol == PWT_DIRICHLET) {
+          a0 = sqrt(Rl(2) * w);
+          a1 = sqrt(Rl(2) * (Rl(1) - w));
+        } else {
+          a0 = Rl(1.41421356237309504880) * w;
+          a1 = Rl(1.41421356237309504880) * (Rl(1) - w);
+        }
+        const C ph = cconj(wavelet_phase<C, true, true>(L, cur[i]));
+        sym[(4 * f + 0) * NT + tid] = a0;
+        sym[(4 * f + 1) * NT + tid] = a1;
+        sym[(4 * f + 2) * NT + tid] = ph.x;
+        sym[(4 * f + 3) * NT + tid] = ph.y;
+        int sl = 0, str = 1;
+#pragma unroll
+        for (int r = 3; r >= 0; --r)
+          if (r < L.d) {
+            sl += cur[i][r] * str;
+            str *= L.HNext[r];
+          }
+        osl[f * NT + tid] = sl;
+      }
+      // the members of this level's fibres: the fibres of level k - 1 (for
+      // k = 0, the input slots); highest first, so that cur[i] is read
+      // before cur[2 i], cur[2 i + 1] overwrite it
+#pragma unroll
+      for (int i = (1 << (F - 1 - k)) - 1; i >= 0; --i) {
+        int h1[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) h1[r] = cur[i][r] + (r < L.d ? L.shift1[r] : 0);
+        box_fix(L.HM, h1);
+        if (k == 0) {
+          int s0 = 0, s1 = 0;
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (r < L.d) {
+              s0 += cur[i][r] * L.HM.stride[r];
+              s1 += h1[r] * L.HM.stride[r];
+            }
+          isl[(2 * i) * NT + tid] = s0;
+          isl[(2 * i + 1) * NT + tid] = s1;
+        } else {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            cur[2 * i + 1][r] = h1[r];
+            cur[2 * i][r] = cur[i][r];
+          }
+        }
+      }
+    }
+    const Rl r2 = Rl(0.70710678118654752440);
+    for (int bb = 0; bb < nb; bb += SG) {
+      C v[SG][2 * NL];
+#pragma unroll
+      for (int j = 0; j < SG; ++j)
+        if (j == 0 || bb + j < nb) {
+#pragma unroll
+          for (int i = 0; i < 2 * NL; ++i)
+            v[j][i] = cin[(long long)(b0 + bb + j) * lv[0].mM + isl[i * NT + tid]];
+        }
+#pragma unroll
+      for (int k = 0; k < F; ++k) {
+#pragma unroll
+        for (int i = 0; i < (1 << (F - 1 - k)); ++i) {
+          const int f = (1 << (F - 1 - k)) - 1 + i;
+          const Rl a0 = sym[(4 * f + 0) * NT + tid], a1 = sym[(4 * f + 1) * NT + tid];
+          const C ph = cmake<C>(sym[(4 * f + 2) * NT + tid], sym[(4 * f + 3) * NT + tid]);
+          const int os = osl[f * NT + tid];
+#pragma unroll
+          for (int j = 0; j < SG; ++j)
+            if (j == 0 || bb + j < nb) {
+              const C c0 = v[j][2 * i], c1 = v[j][2 * i + 1];
+              const C d1 = cscale(cadd(cscale(c0, a0), cscale(c1, a1)), r2);
+              const C d2 = cscale(cmul(ph, csub(cscale(c0, a1), cscale(c1, a0))), r2);
+              wout[k][(long long)(b0 + bb + j) * lv[k].mN + os] = d2;
+              v[j][i] = d1;
+            }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < SG; ++j)
+        if (j == 0 || bb + j < nb) sout[(long long)(b0 + bb + j) * Lt.mN + gs] = v[j][0];
+    }
+  }
+}
+
 // Launch shape of split_kernel: enough fibre CTAs for about 8 resident waves,
 // and the signals split into chunks only when the fibres alone are too few.
 inline void split_grid(long long mN, int batch, unsigned& gx, unsigned& gy, int& chunk) {
