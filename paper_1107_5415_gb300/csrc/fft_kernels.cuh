@@ -318,16 +318,6 @@ template <typename C, int EPT, bool COLS, bool POW2, bool PAD, bool TCK>
 __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ tw) {
   int i = 0;
   constexpr bool kC64 = sizeof(C) == 8 && TCK;  // TCK = false: no tensor-core code in the kernel
-  uint32_t* tab32 = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(sm) + a.tc_off);
-  uint32_t* tab16 = tab32 + (a.cnt[kTC32Region] ? tc_words<32>() : 0);
-  if constexpr (kC64) {
-    if (a.tc) {
-      const float2* twf = reinterpret_cast<const float2*>(tw);
-      if (a.cnt[kTC32Region]) tc_build_tables<32>(tab32, twf, a.tw_n);
-      if (a.cnt[0]) tc_build_tables<16>(tab16, twf, a.tw_n);
-      __syncthreads();
-    }
-  }
   if constexpr (!POW2) {
     _Pragma("unroll 1") for (int q = 0; q < a.cnt[kDirectRegion]; ++q, ++i)
         run_direct_stage<C, EPT, COLS, PAD>(sm, a, a.st[i], tw);
@@ -336,17 +326,50 @@ __device__ void run_all_stages(C* sm, const PassArgs& a, const C* __restrict__ t
   _Pragma("unroll 1") for (int q = 0; q < a.cnt[IDX]; ++q, ++i)                  \
       run_stage<C, RR, (EPT / RR > 0 ? EPT / RR : 1), COLS, PAD>(sm, a, a.st[i], tw);
   bool tc16 = false;
+#if defined(__CUDA_ARCH__)
   if constexpr (kC64) {
     if (a.tc) {
-      float2* smf = reinterpret_cast<float2*>(sm);
+      // W tables, mbarrier and tensor memory (fft_tc.cuh), then the radix-32
+      // and radix-16 stages on the tensor cores
+      TcCtx cx;
+      cx.base = reinterpret_cast<unsigned char*>(sm);
+      cx.lay = tc_layout(a.tc_off, a.cnt[kTC32Region] > 0, a.cnt[0] > 0, a.T * a.L / 16);
+      cx.phase = 0;
+      cx.ok = 1;
+      const int cols = tc_tmem_cols(a.T * a.L, a.cnt[kTC32Region] > 0, a.cnt[0] > 0);
       const float2* twf = reinterpret_cast<const float2*>(tw);
+      if (a.cnt[kTC32Region]) tc_build_w<32>(cx.base + cx.lay.w32, twf, a.tw_n);
+      if (a.cnt[0]) tc_build_w<16>(cx.base + cx.lay.w16, twf, a.tw_n);
+      uint32_t* tslot = reinterpret_cast<uint32_t*>(cx.base + cx.lay.taddr);
+      if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc_smem_u32(cx.base + cx.lay.bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+      }
+      if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc_smem_u32(tslot)),
+                     "r"(cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+      }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // W tables -> tensor-core reads
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      cx.tmem = *tslot;
+      float2* smf = reinterpret_cast<float2*>(sm);
       _Pragma("unroll 1") for (int q = 0; q < a.cnt[kTC32Region]; ++q, ++i)
-          run_tc_stage<32, COLS, PAD>(smf, a, a.st[i], twf, tab32);
+          run_tc_stage<32, COLS, PAD>(smf, a, a.st[i], twf, cx);
       _Pragma("unroll 1") for (int q = 0; q < a.cnt[0]; ++q, ++i)
-          run_tc_stage<16, COLS, PAD>(smf, a, a.st[i], twf, tab16);
+          run_tc_stage<16, COLS, PAD>(smf, a, a.st[i], twf, cx);
       tc16 = true;
+      // every stage ends with tcgen05.fence::before_thread_sync and a barrier
+      if (threadIdx.x < 32) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(cx.tmem), "r"(cols) : "memory");
+      }
     }
   }
+#endif
   if (!tc16) {
     PFFT_REGION(16, 0)
   }

@@ -12,6 +12,7 @@
 
 #include "../../include/pfft.h"
 #include "fft_plan.hpp"
+#include "fft_tc.cuh"
 #include "lattice.hpp"
 #include "plan_common.hpp"
 #include "plan_internal.hpp"
@@ -285,9 +286,20 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
   p.smem_bytes = int(size_t(p.dir_off + 2 * rmax) * elem_bytes(P.dtype));
   p.tc = P.tc ? 1 : 0;
   p.tc_off = (p.smem_bytes + 15) & ~15;
-  if (p.tc) {  // fragment tables of the radix-32 / 16 tensor-core stages (fft_tc.cuh)
-    const int w32 = 2 * 16 * 32 * 4, w16 = 2 * 4 * 32 * 4;
-    p.smem_bytes = p.tc_off + 4 * ((p.cnt[kTC32Region] ? w32 : 0) + (p.cnt[0] ? w16 : 0));
+  if (p.tc) {  // tensor-core stages (fft_tc.cuh)
+    // the hi / lo rows of a stage's 128-butterfly chunks overwrite the tile
+    for (int i = 0; i < p.nstages; ++i) {
+      const int R = p.st[i].R;
+      if (R != 16 && R != 32) continue;
+      const int nch = (T * p.L / R + 127) / 128;
+      p.tc_off = std::max(p.tc_off, nch * tc_chunk_bytes(R));
+    }
+    p.tc_off = (p.tc_off + 15) & ~15;
+    p.smem_bytes = tc_layout(p.tc_off, p.cnt[kTC32Region] > 0, p.cnt[0] > 0, T * p.L / 16).end;
+    // every warp of a lane quarter reads its rows of the accumulator: whole warp quadruples
+    p.nthreads = (p.nthreads + 127) / 128 * 128;
+    if (p.nthreads > kMaxThreads || tc_tmem_cols(T * p.L, p.cnt[kTC32Region] > 0, p.cnt[0] > 0) > 256)
+      return PFFT_ERR_UNSUPPORTED;
   }
   if (p.smem_bytes > 227 * 1024) return PFFT_ERR_UNSUPPORTED;
   return PFFT_OK;

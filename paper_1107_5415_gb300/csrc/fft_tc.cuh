@@ -1,42 +1,154 @@
-// Split-precision tensor-core stages of radix 16 and 32 (complex64 only).
+// Split-precision tensor-core stages of radix 16 and 32 (complex64 only), on
+// the fifth-generation tensor cores (tcgen05.mma, accumulators in tensor
+// memory).
 //
 // A Stockham stage of radix R is, per butterfly, the dense product
 // y = F x' with F[s][r] = omega_R^{s r} and x' the twiddled inputs.  In real
-// arithmetic this is the 2R x 2R matrix [[Fr, -Fi], [Fi, Fr]] applied to
-// [Re x'; Im x'], and the butterflies of a tile are its columns: a GEMM with
-// M = K = 2R and N = the butterflies, run with mma.sync m16n8k16 (one warp,
-// eight butterflies per N-tile).  Both operands are split into fp16 halves,
-// a = a_hi + a_lo with a_hi = fp16(a) and a_lo = fp16(a - a_hi), and the
-// product is accumulated in fp32 as a_hi b_hi + a_hi b_lo + a_lo b_hi, which
-// keeps about 22 significant bits (the dropped a_lo b_lo term is below the
-// fp32 rounding of the sums).  Each butterfly is scaled by a power of two
-// before the split so that its largest input lies in [2^10, 2^11) (the four
-// lanes holding its inputs agree on the factor through two shuffles), and its
-// outputs are scaled back after the accumulation: both steps are exact in
-// fp32, so the fp16 halves neither overflow nor fall into the subnormal range
-// for data of any magnitude from 2^-116 up to the fp32 range.
+// arithmetic [Re y; Im y] = W [Re x'; Im x'] with the 2R x 2R matrix
+// W = [[Fr, -Fi], [Fi, Fr]].  The butterflies of a stage, 128 at a time, are
+// the rows of the operand A (M = 128, K = 2R: row m holds [Re x'; Im x'] of
+// butterfly m), W^T is the operand B (K x N, N = 2R), and D = A B holds the
+// outputs of butterfly m in row m, which is lane m of the tensor memory.
 //
-// The A operand (the DFT matrix) is the same for every butterfly: each CTA
-// writes its fragments, hi and lo, to shared memory once, in the register
-// order of the m16n8k16 A fragment, so that a lane fetches its four
-// registers of a tile with one 16-byte load.
+// Both operands are split into fp16 halves, a = a_hi + a_lo with
+// a_hi = fp16(a) and a_lo = fp16(a - a_hi), and the three products
+// A_hi B_hi + A_hi B_lo + A_lo B_hi are chained into one fp32 accumulator
+// (kind::f16), which keeps about 22 significant bits (the dropped
+// A_lo B_lo term is below the fp32 rounding of the sums).  Each butterfly is
+// scaled by a power of two before the split so that its largest input lies
+// in [2^10, 2^11), and its outputs are scaled back after the accumulation:
+// both steps are exact in fp32, so the fp16 halves neither overflow nor fall
+// into the subnormal range for data of any magnitude from 2^-116 up to the
+// fp32 range.  One thread holds whole butterflies (32 / R of them), so the
+// scale needs no lane exchange.
+//
+// Per stage: every thread gathers and twiddles its butterflies from the tile;
+// after a barrier it writes their hi and lo rows over the tile (the staging
+// takes the tile's 8 bytes per point: 2R fp16 values twice per butterfly of
+// R points), in the canonical K-major layout without swizzle (core matrices
+// of 8 rows x 16 bytes, adjacent along K, 8-row groups 2R x 16 bytes apart).
+// One thread issues the 3 x 2R / 16 MMAs of every 128-butterfly chunk, each
+// chunk into its own 2R tensor-memory columns, and commits them to an
+// mbarrier; after the bounded wait every warp reads its lane quarter of D
+// with tcgen05.ld, undoes the scale and writes the outputs into the tile.
+// W's hi and lo halves are staged once per CTA in shared memory.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include "fft_plan.hpp"
 
 namespace pfft {
 
-template <int R>
-__host__ __device__ constexpr int tc_tiles() {
-  return (2 * R / 16) * (2 * R / 16);
+// Byte offset of element (row, k) of a K-major fp16 operand with K columns:
+// core matrices of 8 rows x 16 bytes, the core matrices of one 8-row group
+// adjacent along K (128 bytes apart), 8-row groups K x 16 bytes apart.
+__host__ __device__ constexpr uint32_t tc_kmajor_off(int row, int k, int K) {
+  return uint32_t((row >> 3) * (K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
-// 32-bit words of the hi and lo fragment tables of radix R
-template <int R>
-__host__ __device__ constexpr int tc_words() {
-  return 2 * tc_tiles<R>() * 32 * 4;
+// Bytes of one operand half (hi or lo): rows x K fp16.
+__host__ __device__ constexpr int tc_half_bytes(int rows, int K) { return rows * K * 2; }
+// Shared-memory bytes of W (hi and lo) for radix R.
+__host__ __device__ constexpr int tc_w_bytes(int R) { return 2 * tc_half_bytes(2 * R, 2 * R); }
+// Staging bytes of one 128-butterfly chunk (hi and lo rows of A).
+__host__ __device__ constexpr int tc_chunk_bytes(int R) { return 2 * tc_half_bytes(128, 2 * R); }
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading-dimension
+// byte offset (between core matrices adjacent along K), stride-dimension byte
+// offset (between 8-row groups), all in 16-byte units; bits 46-48 hold the
+// fixed value 0b001; base offset 0, no swizzle.
+__host__ __device__ constexpr uint64_t tc_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((saddr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
 }
+// Instruction descriptor of kind::f16: fp32 accumulator (bits 4-5 = 1), A
+// and B fp16 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N / 8 in
+// bits 17-22, M / 16 in bits 24-28.
+__host__ __device__ constexpr uint32_t tc_instr_desc(int M, int N) {
+  return (1u << 4) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// Shared-memory layout of the tensor-core context (planner and kernel):
+// [W32 hi | W32 lo] [W16 hi | W16 lo] [scale exponents, int8, one per
+// butterfly] [mbarrier] [tensor-memory address]
+struct TcLayout {
+  int w32, w16, ex, bar, taddr, end;
+};
+__host__ __device__ inline TcLayout tc_layout(int base, bool has32, bool has16, int max_bfly) {
+  TcLayout t;
+  t.w32 = base;
+  t.w16 = t.w32 + (has32 ? tc_w_bytes(32) : 0);
+  t.ex = t.w16 + (has16 ? tc_w_bytes(16) : 0);
+  t.bar = (t.ex + max_bfly + 15) & ~15;
+  t.taddr = t.bar + 8;
+  t.end = t.bar + 16;
+  return t;
+}
+// Tensor-memory columns of a pass: a stage of radix R keeps 2R fp32 columns
+// per 128-butterfly chunk (T L / R butterflies); the largest of the pass's
+// tensor-core stages, as a power of two >= 32.
+__host__ __device__ inline int tc_tmem_cols(int points, bool has32, bool has16) {
+  int need = 0;
+  if (has32) need = ((points / 32 + 127) / 128) * 64;
+  if (has16) need = need > ((points / 16 + 127) / 128) * 32 ? need : ((points / 16 + 127) / 128) * 32;
+  int c = 32;
+  while (c < need) c <<= 1;
+  return c;
+}
+
+#if defined(__CUDA_ARCH__)
+__device__ __forceinline__ uint32_t tc_smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool tc_mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t tc_globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Bounded wait: at most `limit` tries and about one second.
+__device__ __forceinline__ bool tc_mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t limit) {
+  const uint64_t t0 = tc_globaltimer();
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (tc_mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && tc_globaltimer() - t0 > 1000000000ull) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// One D += A B (or D = A B when acc == 0), M = 128, operands in shared memory.
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+               : "memory");
+}
+// 16 consecutive fp32 columns of this thread's lane (warp-wide).
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
 // Two fp32 values -> packed fp16 pairs (hi, lo); the first value in the low half.
 __device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
@@ -47,64 +159,59 @@ __device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& hi, uint3
   lo = uint32_t(__half_as_ushort(l0)) | (uint32_t(__half_as_ushort(l1)) << 16);
 }
 
-__device__ __forceinline__ void mma_f16_16816(float* d, const uint4& a, uint32_t b0, uint32_t b1) {
-  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
-}
-
-// Fragment tables of the real DFT matrix of radix R: words [hl][tile][lane][4]
-// (hl = 0: hi, 1: lo; tile = mt * KT + kt).  Register q of lane (g, t) of a
-// tile holds rows 16 mt + g (+8 if q odd) and columns 16 kt + 2t, +1 (+8 if q >= 2).
+// W of radix R, hi and lo, as the K-major operand B (row n = output n of
+// [Re y; Im y], column k = input k of [Re x; Im x]).
 template <int R>
-__device__ void tc_build_tables(uint32_t* tab, const float2* __restrict__ tw, int tw_n) {
-  constexpr int KT = 2 * R / 16;
-  constexpr int n = tc_tiles<R>() * 32 * 4;
+__device__ void tc_build_w(unsigned char* wsm, const float2* __restrict__ tw, int tw_n) {
+  constexpr int K = 2 * R;
   const int wstride = tw_n / R;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int tile = e >> 7, lane = (e >> 2) & 31, reg = e & 3;
-    const int mt = tile / KT, kt = tile - (tile / KT) * KT;
-    const int g = lane >> 2, t = lane & 3;
-    const int row = 16 * mt + g + ((reg & 1) ? 8 : 0);
-    const int col = 16 * kt + 2 * t + ((reg & 2) ? 8 : 0);
+  for (int e = threadIdx.x; e < K * K / 2; e += blockDim.x) {
+    const int n = e / (K / 2), k = 2 * (e - n * (K / 2));
     float v[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      const int cc = col + c;
-      const int s = row % R, r = cc % R;
+      const int kk = k + c;
+      const int s = n % R, r = kk % R;
       const float2 f = __ldg(tw + ((s * r) % R) * wstride);  // omega_R^{s r} = Fr + i Fi
-      const bool yi = row >= R, xi = cc >= R;
+      const bool yi = n >= R, xi = kk >= R;
       v[c] = (yi == xi) ? f.x : (xi ? -f.y : f.y);
     }
     uint32_t hi, lo;
     split_h2(v[0], v[1], hi, lo);
-    tab[e] = hi;
-    tab[n + e] = lo;
+    const uint32_t off = tc_kmajor_off(n, k, K);
+    *reinterpret_cast<uint32_t*>(wsm + off) = hi;
+    *reinterpret_cast<uint32_t*>(wsm + tc_half_bytes(K, K) + off) = lo;
   }
 }
 
-// One Stockham stage of radix R (16 or 32) on the tensor cores; the same
-// index walk as run_stage (fft_kernels.cuh).  Warp w takes the N-tiles
-// (groups of eight consecutive butterflies) w, w + nwarps, ...; at most
-// G = 128 / R per warp, which holds when the block has >= T L / 32 threads.
-// All reads of the stage happen before the barrier, all writes after it.
+// Per-pass tensor-core state: shared-memory layout, the tensor-memory base
+// and the mbarrier phase.
+struct TcCtx {
+  unsigned char* base;  // dynamic shared memory
+  TcLayout lay;
+  uint32_t tmem;        // tensor-memory address of column 0, lane 0
+  uint32_t phase;
+  int ok;               // 0 once a wait has timed out (later stages skip the tensor cores)
+};
+
+// One Stockham stage of radix R (16 or 32) on the tensor cores; the same index
+// walk as run_stage (fft_kernels.cuh).  Thread t takes butterflies t, t + n,
+// ... (at most 32 / R); the planner's thread count guarantees it.  All reads
+// of the tile happen before the first barrier, all writes of outputs after
+// the MMAs have completed.
 template <int R, bool COLS, bool PAD>
 __device__ __noinline__ void run_tc_stage(float2* sm, const PassArgs& a, const StageDesc& s,
-                                          const float2* __restrict__ tw, const uint32_t* tab) {
-  constexpr int MT = 2 * R / 16, KT = MT, HALF = MT / 2;
-  constexpr int G = 128 / R;
-  constexpr int NR = 2 * R / 8;  // inputs r of one butterfly held by a lane
+                                          const float2* __restrict__ tw, TcCtx& cx) {
+  constexpr int K = 2 * R;
+  constexpr int NB = 32 / R;
+  constexpr int CHB = tc_chunk_bytes(R);
   const int per_pencil = a.L / R;
   const int nbf = a.T * per_pencil;
-  const int ngrp = (nbf + 7) >> 3;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
+  const int nthr = blockDim.x;
   const int escale = COLS ? a.T : 1;
   const int step = s.sigma * escale;
   const int istep = s.aR * step;
-  const uint4* ahi = reinterpret_cast<const uint4*>(tab);
-  const uint4* alo = ahi + tc_tiles<R>() * 32;
+  signed char* exs = reinterpret_cast<signed char*>(cx.base + cx.lay.ex);
   auto locate = [&](int b, int& ebase, int& k, int& j) {
     int tt, rest;
     if (COLS) {
@@ -121,96 +228,128 @@ __device__ __noinline__ void run_tc_stage(float2* sm, const PassArgs& a, const S
     k = j - s.div_Ns.div(j) * s.Ns;
     ebase = COLS ? base * a.T + tt : tt * a.L + base;
   };
-  float acc[G][MT][4];
-  int ex_of[G];
+  // ---- gather, twiddle, scale
+  float x[NB][K];
+  int ex[NB];
 #pragma unroll
-  for (int u = 0; u < G; ++u) {
-    ex_of[u] = 0;
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[u][mt][c] = 0.f;
-    const int grp = warp + u * nw;
-    if (grp >= ngrp) continue;  // warp-uniform
-    float xr[NR], xi[NR];
-    const int bf = grp * 8 + g;
+  for (int u = 0; u < NB; ++u) {
+    const int bf = threadIdx.x + u * nthr;
+    ex[u] = 0;
     if (bf < nbf) {
       int ebase, k, j;
       locate(bf, ebase, k, j);
       const int i0 = ebase + j * step;
+      float mx = 0.f;
 #pragma unroll
-      for (int q = 0; q < NR; ++q) {
-        const int r = (q >> 2) * 16 + 2 * t + (q & 1) + ((q & 2) ? 8 : 0);
-        float2 x = sm[phys<PAD>(i0 + r * istep)];
-        if (s.Ns > 1) x = cmul(x, __ldg(tw + (k * r) * s.twstep));  // k r < Ns R: no reduction
-        xr[q] = x.x;
-        xi[q] = x.y;
+      for (int r = 0; r < R; ++r) {
+        float2 v = sm[phys<PAD>(i0 + r * istep)];
+        if (s.Ns > 1 && r > 0) v = cmul(v, __ldg(tw + (k * r) * s.twstep));  // k r < Ns R: no reduction
+        x[u][r] = v.x;
+        x[u][R + r] = v.y;
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
       }
-    } else {
+      int e = mx > 0.f ? 10 - ilogbf(mx) : 0;
+      e = e > 126 ? 126 : (e < -126 ? -126 : e);  // 2^e and 2^-e both normal
+      ex[u] = e;
+      const float up = __int_as_float((127 + e) << 23);
 #pragma unroll
-      for (int q = 0; q < NR; ++q) xr[q] = xi[q] = 0.f;
+      for (int i = 0; i < K; ++i) x[u][i] *= up;
     }
-    // power-of-two scale of this butterfly (lanes 4 g .. 4 g + 3 hold its inputs)
-    float mx = 0.f;
-#pragma unroll
-    for (int q = 0; q < NR; ++q) mx = fmaxf(mx, fmaxf(fabsf(xr[q]), fabsf(xi[q])));
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-    int ex = mx > 0.f ? 10 - ilogbf(mx) : 0;
-    ex = ex > 126 ? 126 : (ex < -126 ? -126 : ex);  // 2^ex and 2^-ex both normal
-    ex_of[u] = ex;
-    const float up = __int_as_float((127 + ex) << 23);
-#pragma unroll
-    for (int q = 0; q < NR; ++q) {
-      xr[q] *= up;
-      xi[q] *= up;
-    }
-    uint32_t bh[KT][2], bl[KT][2];
-#pragma unroll
-    for (int kt = 0; kt < KT; ++kt) {
-      const int qb = (kt % HALF) * 4;
-      const float* src = kt < HALF ? xr : xi;
-      split_h2(src[qb + 0], src[qb + 1], bh[kt][0], bl[kt][0]);
-      split_h2(src[qb + 2], src[qb + 3], bh[kt][1], bl[kt][1]);
-    }
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-      for (int kt = 0; kt < KT; ++kt) {
-        const uint4 ah = ahi[(mt * KT + kt) * 32 + lane];
-        const uint4 al = alo[(mt * KT + kt) * 32 + lane];
-        mma_f16_16816(acc[u][mt], ah, bh[kt][0], bh[kt][1]);
-        mma_f16_16816(acc[u][mt], ah, bl[kt][0], bl[kt][1]);
-        mma_f16_16816(acc[u][mt], al, bh[kt][0], bh[kt][1]);
-      }
   }
+  __syncthreads();  // every read of the tile is done: the staging may overwrite it
+  // ---- hi / lo rows of A over the tile
+  unsigned char* stg = reinterpret_cast<unsigned char*>(sm);
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int bf = threadIdx.x + u * nthr;
+    if (bf < nbf) {
+      unsigned char* ch = stg + (bf >> 7) * CHB;
+      const int m = bf & 127;
+      exs[bf] = static_cast<signed char>(ex[u]);
+#pragma unroll
+      for (int kg = 0; kg < K / 8; ++kg) {
+        uint4 h, l;
+        split_h2(x[u][8 * kg + 0], x[u][8 * kg + 1], h.x, l.x);
+        split_h2(x[u][8 * kg + 2], x[u][8 * kg + 3], h.y, l.y);
+        split_h2(x[u][8 * kg + 4], x[u][8 * kg + 5], h.z, l.z);
+        split_h2(x[u][8 * kg + 6], x[u][8 * kg + 7], h.w, l.w);
+        const uint32_t off = tc_kmajor_off(m, 8 * kg, K);
+        *reinterpret_cast<uint4*>(ch + off) = h;
+        *reinterpret_cast<uint4*>(ch + tc_half_bytes(128, K) + off) = l;
+      }
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic-proxy writes -> tensor-core reads
   __syncthreads();
+  const int nch = (nbf + 127) >> 7;
+  const uint32_t bar = tc_smem_u32(cx.base + cx.lay.bar);
+  if (threadIdx.x == 0 && cx.ok) {
+    tc_fence_after();
+    constexpr uint32_t idesc = tc_instr_desc(128, K);
+    const uint32_t wb = tc_smem_u32(cx.base + (R == 32 ? cx.lay.w32 : cx.lay.w16));
+    const uint32_t sb = tc_smem_u32(stg);
+    for (int c = 0; c < nch; ++c) {
+      const uint32_t ahi = sb + c * CHB, alo = ahi + tc_half_bytes(128, K);
+      const uint32_t dt = cx.tmem + uint32_t(c * K);
+#pragma unroll
+      for (int kk = 0; kk < K / 16; ++kk) {
+        const uint64_t dah = tc_smem_desc(ahi + kk * 256, 128, K * 16);
+        const uint64_t dal = tc_smem_desc(alo + kk * 256, 128, K * 16);
+        const uint64_t dbh = tc_smem_desc(wb + kk * 256, 128, K * 16);
+        const uint64_t dbl = tc_smem_desc(wb + tc_half_bytes(K, K) + kk * 256, 128, K * 16);
+        tc_mma(dt, dah, dbh, idesc, kk > 0 ? 1u : 0u);
+        tc_mma(dt, dah, dbl, idesc, 1u);
+        tc_mma(dt, dal, dbh, idesc, 1u);
+      }
+    }
+    tc_commit(bar);
+  }
+  // ---- wait for the products (bounded), then read D back
+  bool done = cx.ok != 0;
+  if (done) {
+    done = tc_mbar_wait_bounded(bar, cx.phase, a.spin_limit);
+    if (!done) {
+      if (threadIdx.x == 0) atomicExch(a.status, 8);  // PFFT_ERR_TIMEOUT
+      tc_mbar_wait_bounded(bar, cx.phase, kSpinLimit);  // let the products in flight finish
+    }
+    cx.phase ^= 1u;
+  }
+  done = __syncthreads_and(done ? 1 : 0) != 0;
+  if (!done) cx.ok = 0;
+  tc_fence_after();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = nthr >> 5;
+  const int q = warp & 3;
   const int ostep = s.Ns * step;
-#pragma unroll
-  for (int u = 0; u < G; ++u) {
-    const int grp = warp + u * nw;
-    if (grp >= ngrp) continue;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {  // D columns 2t, 2t + 1
-      const int bf = grp * 8 + 2 * t + c;
-      // undo the scale of butterfly 2t + c (held by lane 4 (2t + c))
-      const int ex = __shfl_sync(0xffffffffu, ex_of[u], (2 * t + c) * 4);
-      const float down = __int_as_float((127 - ex) << 23);
-      if (bf >= nbf) continue;
+  for (int c = warp >> 2; c < nch; c += nw >> 2) {
+    const uint32_t ta = cx.tmem + (uint32_t(32 * q) << 16) + uint32_t(c * K);
+    const int bf = c * 128 + 32 * q + lane;
+    const bool mine = bf < nbf && done;
+    int ob = 0;
+    float down = 0.f;
+    if (mine) {
       int ebase, k, j;
       locate(bf, ebase, k, j);
-      const int ob = ebase + ((j - k) * R + k) * step;
+      ob = ebase + ((j - k) * R + k) * step;
+      down = __int_as_float((127 - int(exs[bf])) << 23);
+    }
+    // outputs 16 h .. 16 h + 15: real parts in columns 16 h.., imaginary parts in R + 16 h..
 #pragma unroll
-      for (int mt = 0; mt < HALF; ++mt)
+    for (int h = 0; h < R / 16; ++h) {
+      uint32_t re[16], im[16];
+      tc_ld16(ta + 16 * h, re);
+      tc_ld16(ta + R + 16 * h, im);
+      tc_wait_ld();
+      if (mine) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {  // D rows g, g + 8
-          const int so = 16 * mt + g + 8 * h;
-          sm[phys<PAD>(ob + so * ostep)] =
-              make_float2(acc[u][mt][2 * h + c] * down, acc[u][mt + HALF][2 * h + c] * down);
-        }
+        for (int so = 0; so < 16; ++so)
+          sm[phys<PAD>(ob + (16 * h + so) * ostep)] =
+              make_float2(__uint_as_float(re[so]) * down, __uint_as_float(im[so]) * down);
+      }
     }
   }
+  tc_fence_before();
   __syncthreads();
 }
+#endif  // __CUDA_ARCH__
 
 }  // namespace pfft
