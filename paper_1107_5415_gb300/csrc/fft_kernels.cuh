@@ -577,17 +577,18 @@ __device__ __forceinline__ void col_pass_body(const PassArgs& a, int tile, int s
 }
 
 // MINB: resident CTAs per SM the register allocation is fitted to (2 for the
-// 16-points-per-thread build, whose tiles hold at most 8192 points).
+// 16-points-per-thread build, whose tiles hold at most 8192 points).  Only the
+// 32-points-per-thread build carries the tensor-core stages.
 template <typename C, int EPT, bool POW2, bool PAD, int MINB = 1>
 __global__ void __launch_bounds__(kMaxThreads, MINB) row_pass_kernel(PassArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  row_pass_body<C, EPT, POW2, PAD>(a, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
+  row_pass_body<C, EPT, POW2, PAD, EPT == 32>(a, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
 }
 
 template <typename C, int EPT, bool POW2, bool PAD, int MINB = 1>
 __global__ void __launch_bounds__(kMaxThreads, MINB) col_pass_kernel(PassArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  col_pass_body<C, EPT, POW2, PAD>(a, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
+  col_pass_body<C, EPT, POW2, PAD, EPT == 32>(a, blockIdx.x, blockIdx.y, reinterpret_cast<C*>(smem_raw));
 }
 
 // Allow the largest dynamic shared-memory size and prefer the maximum shared

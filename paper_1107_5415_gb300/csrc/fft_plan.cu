@@ -286,7 +286,8 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
   p.smem_bytes = int(size_t(p.dir_off + 2 * rmax) * elem_bytes(P.dtype));
   p.tc = P.tc ? 1 : 0;
   p.tc_off = (p.smem_bytes + 15) & ~15;
-  if (p.tc) {  // tensor-core stages (fft_tc.cuh)
+  if (p.tc) {  // tensor-core stages (fft_tc.cuh), in the 32-points-per-thread kernels only
+    if (p.ept != 32) return PFFT_ERR_UNSUPPORTED;
     // the hi / lo rows of a stage's 128-butterfly chunks overwrite the tile
     for (int i = 0; i < p.nstages; ++i) {
       const int R = p.st[i].R;

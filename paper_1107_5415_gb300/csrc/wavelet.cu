@@ -104,6 +104,7 @@ struct pwt_plan_s {
   std::vector<IMat> boxes;    // H(M_l^T)
   std::vector<LevelDesc> lv;  // device descriptors
   LevelDesc* dlv = nullptr;   // the same in device memory (fused launches)
+  void* symtab = nullptr;     // per-fibre symbols of the levels that fused launches take
   void* tables = nullptr;     // phase tables of all levels
   void* ws[2] = {nullptr, nullptr};
   Profiler prof;
@@ -115,6 +116,7 @@ static void release(pwt_plan_s* P) {
   if (!P) return;
   if (P->tables) cudaFree(P->tables);
   if (P->dlv) cudaFree(P->dlv);
+  if (P->symtab) cudaFree(P->symtab);
   for (auto p : P->ws)
     if (p) cudaFree(p);
   delete P;
@@ -377,6 +379,26 @@ static pfft_status plan_device(pwt_plan_s& P) {
     else
       phase_table_kernel<double2><<<grd, blk>>>((double2*)L.tab_lo, (double2*)L.tab_hi, L.q, nhi);
     if (cudaGetLastError() != cudaSuccess) return PFFT_ERR_CUDA;
+  }
+  // per-fibre symbol tables for the fused launches (complex64, int32 index
+  // paths; for batches of four signals or more, where reading a fibre's
+  // symbols costs less than evaluating them in every chunk of signals)
+  if (P.dtype == PFFT_C64 && P.levels > 1 && P.batch >= 4) {
+    size_t n = 0;
+    for (auto& L : P.lv)
+      if (L.small) n += size_t(L.mN);
+    if (n) {
+      if (int e_ = device_alloc(&P.symtab, n * sizeof(float4))) return pfft_status(e_);
+      float4* t = static_cast<float4*>(P.symtab);
+      for (auto& L : P.lv) {
+        if (!L.small) continue;
+        L.symtab = t;
+        const int grd = int(std::min<long long>((L.mN + 255) / 256, 152LL * 8));
+        symbol_table_kernel<float2><<<grd, 256>>>(L, t);
+        if (cudaGetLastError() != cudaSuccess) return PFFT_ERR_CUDA;
+        t += L.mN;
+      }
+    }
   }
   if (int e_ = device_alloc((void**)&P.dlv, sizeof(LevelDesc) * P.lv.size())) return pfft_status(e_);
   if (cudaMemcpy(P.dlv, P.lv.data(), sizeof(LevelDesc) * P.lv.size(), cudaMemcpyHostToDevice) != cudaSuccess)

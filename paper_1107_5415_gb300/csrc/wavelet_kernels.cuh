@@ -43,6 +43,9 @@ struct LevelDesc {
   int offq;              // multiple of q that makes ph32 . h non-negative
   const void* tab_lo;    // exp(-2 pi i t / q), t < 2^kLoBits
   const void* tab_hi;    // exp(-2 pi i (t << kLoBits) / q)
+  // per-fibre symbols of the fused launches, by slot of G(N^T): float4
+  // (A(h0), A(h1), conjugate phase) for complex64, or null (evaluated in place)
+  const void* symtab;
   // Smith-coordinate order of the coefficients on G(M^T) (first level of a
   // plan created with PWT_FLAG_INPUT_SNF): the slot of h is the row-major
   // index of mu(h) = (MU_j . h mod n_j) over the snf_D non-trivial cycles,
@@ -235,6 +238,42 @@ __global__ void __launch_bounds__(256) split_kernel(LevelDesc L, int batch, int 
                                      MODE == 0 ? d1out + oN : nullptr, MODE == 0 ? d2out + oN : nullptr);
 }
 
+// Symbols of the fibre at box point g: A(h0), A(h1) and the conjugate
+// wavelet phase (the analysis applies conj(e)).
+template <typename C>
+__device__ __forceinline__ void fibre_symbols(const LevelDesc& L, const int* g, decltype(C::x)& a0,
+                                              decltype(C::x)& a1, C& ph) {
+  using Rl = decltype(C::x);
+  const Rl w = fibre_weight<Rl, true>(L, g);
+  if (L.symbol == PWT_DIRICHLET) {
+    a0 = sqrt(Rl(2) * w);
+    a1 = sqrt(Rl(2) * (Rl(1) - w));
+  } else {
+    a0 = Rl(1.41421356237309504880) * w;
+    a1 = Rl(1.41421356237309504880) * (Rl(1) - w);
+  }
+  ph = cconj(wavelet_phase<C, true, true>(L, g));
+}
+
+// The symbol table of one level (int32 index path): one float4 per fibre,
+// by its slot in the box of H(N^T).
+template <typename C>
+__global__ void __launch_bounds__(256) symbol_table_kernel(LevelDesc L, float4* __restrict__ tab) {
+  for (int gs = blockIdx.x * blockDim.x + threadIdx.x; gs < L.mN; gs += gridDim.x * blockDim.x) {
+    int g[4] = {0, 0, 0, 0};
+    int s = gs;
+    for (int r = L.d - 1; r >= 0; --r) {
+      const int qd = L.divHN[r].div(s);
+      g[r] = s - qd * L.HNext[r];
+      s = qd;
+    }
+    float a0, a1;
+    C ph;
+    fibre_symbols<C>(L, g, a0, a1, ph);
+    tab[gs] = make_float4(a0, a1, ph.x, ph.y);
+  }
+}
+
 // ---- Several levels in one launch (the repetition of steps 2-4 at the end
 // of Section 5.3).  After F levels, a fibre g of G(N_F^T) (the last level's
 // output) draws on 2^F coefficients of the first level's input: its two
@@ -243,10 +282,11 @@ __global__ void __launch_bounds__(256) split_kernel(LevelDesc L, int batch, int 
 // butterflies of the tree level by level and writes every wavelet part once
 // and the last scaling part; the scaling parts of the inner levels never
 // leave registers.  The symbols depend on the fibres only: each thread
-// evaluates them once per g (top-down, so that only the box points of the
-// current level are live) into its column of shared-memory tables and
-// applies them to every signal of its chunk, two signals at a time so that
-// the loads of both are in flight together.
+// takes them once per g (top-down, so that only the box points of the
+// current level are live) from the plan's per-fibre symbol table (or
+// evaluates them) into its column of shared-memory tables and applies them
+// to every signal of its chunk, two signals at a time so that the loads of
+// both are in flight together.
 constexpr int kFuseThreads = 128;
 constexpr int kFuseMax = 3;   // levels per launch (4 needs more registers than pays off)
 constexpr int kFuseWaves = 8; // resident waves of CTAs for the fibres
@@ -310,20 +350,6 @@ __global__ void __launch_bounds__(kFuseThreads, 4)
 #pragma unroll
       for (int i = 0; i < (1 << (F - 1 - k)); ++i) {
         const int f = (1 << (F - 1 - k)) - 1 + i;
-        const Rl w = fibre_weight<Rl, true>(L, cur[i]);
-        Rl a0, a1;
-        if (L.symbol == PWT_DIRICHLET) {
-          a0 = sqrt(Rl(2) * w);
-          a1 = sqrt(Rl(2) * (Rl(1) - w));
-        } else {
-          a0 = Rl(1.41421356237309504880) * w;
-          a1 = Rl(1.41421356237309504880) * (Rl(1) - w);
-        }
-        const C ph = cconj(wavelet_phase<C, true, true>(L, cur[i]));
-        sym[(4 * f + 0) * NT + tid] = a0;
-        sym[(4 * f + 1) * NT + tid] = a1;
-        sym[(4 * f + 2) * NT + tid] = ph.x;
-        sym[(4 * f + 3) * NT + tid] = ph.y;
         int sl = 0, str = 1;
 #pragma unroll
         for (int r = 3; r >= 0; --r)
@@ -332,6 +358,24 @@ __global__ void __launch_bounds__(kFuseThreads, 4)
             str *= L.HNext[r];
           }
         osl[f * NT + tid] = sl;
+        Rl a0, a1;
+        C ph;
+        if constexpr (sizeof(Rl) == 4) {
+          if (L.symtab) {
+            const float4 t = __ldg(static_cast<const float4*>(L.symtab) + sl);
+            a0 = t.x;
+            a1 = t.y;
+            ph = cmake<C>(t.z, t.w);
+          } else {
+            fibre_symbols<C>(L, cur[i], a0, a1, ph);
+          }
+        } else {
+          fibre_symbols<C>(L, cur[i], a0, a1, ph);
+        }
+        sym[(4 * f + 0) * NT + tid] = a0;
+        sym[(4 * f + 1) * NT + tid] = a1;
+        sym[(4 * f + 2) * NT + tid] = ph.x;
+        sym[(4 * f + 3) * NT + tid] = ph.y;
       }
       // the members of this level's fibres: the fibres of level k - 1 (for
       // k = 0, the input slots); highest first, so that cur[i] is read
