@@ -7,17 +7,13 @@
 // current one.  Thread (c, p), c < 8, p < 32, holds rows p + 32 k of column
 // c (two radix-32 Stockham stages, as col_fast_ct_kernel).  Shared memory:
 //
-//   S (66 KiB)  forward: the tile, filled with cp.async in 16-byte pieces of
-//               the workspace rows (dense [row][column]); as soon as the
-//               threads have read it the copies of the next tile are issued
-//               into it.  Inverse: the second half of the sheared gather
-//               from the output box, then the padded exchange tile of the
-//               two stages, after which the next tile's second half is
-//               gathered into it;
-//   X (33 KiB)  forward: the exchange between the two stages and the
-//               sheared output, each in two rounds of half a tile.
-//               Inverse: the first half of the gather, issued for the next
-//               tile as soon as the current one has been read;
+//   S (66 KiB)  the tile: forward, filled with cp.async in 16-byte pieces of
+//               the workspace rows (dense [row][column]); inverse, the
+//               sheared gather from the box in walk layout (8-byte pieces).
+//               As soon as the threads have read it the copies of the next
+//               tile are issued into it;
+//   X (33 KiB)  the exchange between the two stages in two rounds of half a
+//               tile, and (forward) the sheared output in two rounds;
 //   Es          the column points of the walk (forward);
 //   stw         the stage twiddles.
 //
@@ -26,6 +22,10 @@
 // makes thread p write and read the register half H = h xor bit 4 of p in
 // round h (warp-uniform), and dropping bit 9 maps each round one-to-one onto
 // 512 rows of the half tile.
+//
+// The inverse direction's gather leans on the L2: while it computes tile n
+// it gathers tile n + 1 into S and prefetches into L2 the lines that tile
+// n + 2 will gather (the start and the end of each row's run of 8 slots).
 //
 // Sheared output in two rounds.  The walk of thread (c, p) visits rows
 // i_j = (i_0 + 32 j) mod 1024, i_0 = p + c alpha mod 1024, and stores row
@@ -137,8 +137,7 @@ __global__ void __launch_bounds__(256, 2) col_pipe_kernel(PassArgs a) {
     copy_points(g, n & 1);
   };
   // inverse: walk steps [16 h, 16 h + 16) of the sheared gather, in walk
-  // layout W[j mod 16][p][c] (word address 512 t + 16 p + 2 c: conflict free),
-  // half 0 into X, half 1 into S
+  // layout W[j][p][c] in S (word address 512 j + 16 p + 2 c: conflict free)
   auto issue_inv = [&](int g, int h, int n) {
     const int b = g / ntile;
     const C* in = in_all + (int64_t)b * a.m;
@@ -149,13 +148,21 @@ __global__ void __launch_bounds__(256, 2) col_pipe_kernel(PassArgs a) {
     load_point<TS>(a.Ctab, ih, z);
     load_point<TS>(a.Ctab, P, cP);
     box_add_t<DIM>(a.boxG, z, et);
-    C* dst = (h ? S : X) + p * T + tcol;
+    C* dst = S + h * 16 * NT + p * T + tcol;
 #pragma unroll 4
     for (int t = 0; t < 16; ++t) {
       cp_async8(dst + t * NT, in + box_slot_t<DIM>(a.boxG, z));
       box_add_t<DIM>(a.boxG, z, cP);
     }
   };
+
+  // inverse: the rows of the column cycle whose runs the L2 prefetch visits
+  // (the same for every tile)
+  int pfp[FWD ? 1 : L / NT][4];
+  if constexpr (!FWD) {
+#pragma unroll
+    for (int q = 0; q < L / NT; ++q) load_point<TS>(a.Ctab, tid + NT * q, pfp[q]);
+  }
 
   if (blockIdx.x < total) {
     if constexpr (FWD) {
@@ -181,44 +188,16 @@ __global__ void __launch_bounds__(256, 2) col_pipe_kernel(PassArgs a) {
       for (int k = 0; k < R; ++k) v[k] = S[(p + P * k) * T + tcol];
       __syncthreads();  // S is read: the next tile may land in it
       if (gn < total) issue_fwd(gn, n + 1);
-      // stage 0 (Ns = 1), exchange in two rounds through X: round h moves
-      // register half H = h xor bit 4 of p (positions 32 p + r written,
-      // p + 32 r' read, split by bit 9 xor bit 4 of the position; bit 9 dropped)
-      dft_pow2<C, R>(v);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h) __syncthreads();  // round 0's reads of X are done
-        if ((h ^ (p >> 4)) & 1)
-          cpipe_x_write<1>(v, X, p, tcol);
-        else
-          cpipe_x_write<0>(v, X, p, tcol);
-        __syncthreads();
-        if ((h ^ (p >> 4)) & 1)
-          cpipe_x_read<1>(v, X, p, tcol);
-        else
-          cpipe_x_read<0>(v, X, p, tcol);
-      }
     } else {
       // register k from walk step j = (k - m0h) mod 32 of walker pw (conjugated input)
 #pragma unroll
       for (int k = 0; k < R; ++k) {
         const int j = (k - m0h) & (R - 1);
-        const C* src = j < 16 ? X + j * NT : S + (j - 16) * NT;
-        v[k] = cconj(src[pw * T + tcol]);
+        v[k] = cconj(S[j * NT + pw * T + tcol]);
       }
-      __syncthreads();  // X and S are read: the first half of the next gather may land in X
-      if (gn < total) issue_inv(gn, 0, n + 1);
-      // stage 0 (Ns = 1), exchange through the padded tile in S
-      dft_pow2<C, R>(v);
-      C* wb = S + ct_phys<LOGT>(p * R) + tcol;
-#pragma unroll
-      for (int r = 0; r < R; ++r) wb[ct_phys<LOGT>(r)] = v[r];
-      __syncthreads();
-      const C* rb = S + ct_phys<LOGT>(p) + tcol;
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = rb[ct_phys<LOGT>(r * P)];
-      __syncthreads();  // S is free: the second half of the next gather may land in it
+      __syncthreads();  // S is read: the next tile's gather may land in it
       if (gn < total) {
+        issue_inv(gn, 0, n + 1);
         issue_inv(gn, 1, n + 1);
         const int gnn = gn + gridDim.x;
         if (gnn < total) {
@@ -232,7 +211,8 @@ __global__ void __launch_bounds__(256, 2) col_pipe_kernel(PassArgs a) {
 #pragma unroll
           for (int q = 0; q < L / NT; ++q) {
             int y[4];
-            load_point<TS>(a.Ctab, tid + NT * q, y);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) y[r] = pfp[q][r];
             box_add_t<DIM>(a.boxG, y, e2);
             const int y0 = box_slot_t<DIM>(a.boxG, y);
             prefetch_l2(in2 + y0);
@@ -240,6 +220,23 @@ __global__ void __launch_bounds__(256, 2) col_pipe_kernel(PassArgs a) {
           }
         }
       }
+    }
+    // stage 0 (Ns = 1), exchange in two rounds through X: round h moves
+    // register half H = h xor bit 4 of p (positions 32 p + r written,
+    // p + 32 r' read, split by bit 9 xor bit 4 of the position; bit 9 dropped)
+    dft_pow2<C, R>(v);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h) __syncthreads();  // round 0's reads of X are done
+      if ((h ^ (p >> 4)) & 1)
+        cpipe_x_write<1>(v, X, p, tcol);
+      else
+        cpipe_x_write<0>(v, X, p, tcol);
+      __syncthreads();
+      if ((h ^ (p >> 4)) & 1)
+        cpipe_x_read<1>(v, X, p, tcol);
+      else
+        cpipe_x_read<0>(v, X, p, tcol);
     }
     // stage 1 (Ns = 32): v[r] = frequency p + 32 r
     if (p) main_twiddle<C, R>(v, stw + a.stw_off[1] + p * 5);

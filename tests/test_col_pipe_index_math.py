@@ -4,9 +4,10 @@ p + 32 k of column c).
 
 The model replays every shared-memory access of the kernel for one tile:
 
-* the dense tile read, the radix-32 stage, the exchange in two rounds
-  through the padded half tile X (round h moves register half
-  h xor bit 4 of p) and the twiddled second stage give each column's
+* the dense tile read (forward) or the walk-layout gather (inverse), the
+  radix-32 stage, the exchange in two rounds through the padded half tile X
+  (both directions; round h moves register half h xor bit 4 of p) and the
+  twiddled second stage give each column's
   1024-point DFT
   (numpy), v[r] of thread (c, p) = frequency p + 32 r;
 * in the two output rounds each slot of X is written once, and the walker
@@ -153,46 +154,33 @@ def test_shared_memory_layout_fits_two_ctas_per_sm():
     assert ct_phys(L) >= S and Es == 32 and per_cta <= 110 * 1024 and 2 * (per_cta + 1024) <= 228 * 1024
 
 
-def test_single_round_exchange_through_the_padded_tile():
-    """The inverse direction exchanges in one round through S: positions
-    32 p + r written and p + 32 r read at ct_phys(position) + c, a bijection
-    onto the padded tile that fits the tile buffer, two wavefronts per warp."""
-    tid = np.arange(256)
-    c, p = tid & 7, tid >> 3
-    w = np.stack([ct_phys(32 * p + r) + c for r in range(R)], axis=1)
-    rd = np.stack([ct_phys(p + 32 * r) + c for r in range(R)], axis=1)
-    for idx in (w, rd):
-        assert len(np.unique(idx)) == L * T and idx.max() < ct_phys(L)
-        for j in range(R):
-            check_banks(idx[:, j])
-    assert set(w.reshape(-1)) == set(rd.reshape(-1))
-
-
 @pytest.mark.parametrize("alpha", [0, 3, 96, 513])
 def test_inverse_gather_in_walk_layout(alpha):
     """Inverse direction: walker (c, p) gathers step j = 16 h + t of its walk
-    (row (i_0 + 32 j) mod 1024 of column c) into W_h[t][p][c] (h = 0: X,
-    h = 1: S); thread (c, p) then finds its register k (row p + 32 k) at
-    step j = (k - m0h) mod 32 of walker pw = (p - c alpha) mod 32 -- every
-    register once, every access conflict free."""
+    (row (i_0 + 32 j) mod 1024 of column c) into W[j][p][c] in S (two halves
+    of 16 steps, issued together); thread (c, p) then finds its register k
+    (row p + 32 k) at step j = (k - m0h) mod 32 of walker pw = (p - c alpha)
+    mod 32 -- every register once, every access conflict free, and the walk
+    layout fits the tile buffer."""
     tid = np.arange(256)
     c, p = tid & 7, tid >> 3
     off = (c * alpha) % L
     i0 = (p + off) % L
-    W = np.full((2, 16, P, T), -1, np.int64)
-    for j in range(32):
-        h, t = divmod(j, 16)
-        rows = (i0 + 32 * j) % L
-        assert (W[h, t, p, c] == -1).all()
-        W[h, t, p, c] = rows * T + c  # the tile element gathered
-        if alpha in (3, 513):
-            check_banks(((t * P + p) * T + c))
+    W = np.full(ct_phys(L), -1, np.int64)  # S holds the padded tile's worth of elements
+    for h in range(2):
+        for t in range(16):
+            j = 16 * h + t
+            rows = (i0 + 32 * j) % L
+            idx = h * 16 * P * T + t * P * T + p * T + c  # S + h 16 NT + t NT + p T + c
+            assert (W[idx] == -1).all()
+            W[idx] = rows * T + c  # the tile element gathered
+            if alpha in (3, 513):
+                check_banks(idx)
     pw = (p - off) & (P - 1)
     m0h = ((pw + off) % L) >> 5
     for k in range(R):
         j = (k - m0h) & 31
-        h, t = j // 16, j % 16
-        got = W[h, t, pw, c]
-        assert (got == (p + P * k) * T + c).all()
+        idx = j * P * T + pw * T + c
+        assert (W[idx] == (p + P * k) * T + c).all()
         if alpha in (3, 513):
-            check_banks((t * P + pw) * T + c)
+            check_banks(idx)
