@@ -225,6 +225,11 @@ enum {
  *            reading: sqrt|det J| times the periodised trapezoid of blend
  *            width eta, 0 < eta < 1; not defined in the paper)
  *   batch, dtype as for pfft_plan_create; flags: 0 or PWT_FLAG_INPUT_SNF.
+ * Device memory owned by the plan: two workspaces of |det M| / 2 * batch
+ * elements (more than one level), the phase tables, and, for complex64 plans
+ * of four or more signals, the per-fibre symbols of every level (16 bytes
+ * per point of G(N_l^T), about 16 |det M| bytes in all), which decompose
+ * reads when it runs up to three levels in one launch.
  * Returns PFFT_ERR_NOT_INTEGRAL if some J_l^{-1} M_l is not integral. */
 pfft_status pwt_plan_create(pwt_plan* out, int d, const int64_t* M, int levels, const int64_t* J,
                             int symbol, double eta, int64_t batch, int dtype, unsigned flags);
