@@ -324,7 +324,16 @@ pfft_status pwt_merge_general(int d, const int64_t* M, const int64_t* J, int64_t
 enum {
   PFFT_BATCH_NO_GRAPH = 1u, /* queue the grouped launches directly instead of replaying a graph */
   PFFT_BATCH_AUTOTUNE = 2u, /* time candidate tile / radix schedules at creation and keep the fastest */
-  PFFT_BATCH_RADIX8 = 4u    /* start from radix-8 power-of-two stages instead of radix 16 */
+  PFFT_BATCH_RADIX8 = 4u,   /* start from radix-8 power-of-two stages instead of radix 16 */
+  /* the whole batch -- every row-pass tile, every column-pass tile, every
+   * split unit -- in ONE kernel launch whose CTAs take work units from a
+   * device queue in dependency order; a column tile waits (bounded) until
+   * its pattern's row tiles are done, a split unit until the pattern's
+   * coefficients are.  Results equal the grouped launches' up to rounding
+   * (every tile runs with 512 threads, which changes how the stage twiddle
+   * powers are formed).  All units share the largest tile's shared memory
+   * (fewer CTAs per SM when one pattern needs a large tile). */
+  PFFT_BATCH_ONE_LAUNCH = 8u
 };
 
 /* n >= 1 patterns; d: host array of n dimensions (1..4); M: host array, the
@@ -360,6 +369,20 @@ pfft_status pfft_batch_schedule(pfft_batch b, int* row_budget, int* col_budget, 
  * time (its workspace is shared). */
 pfft_status pfft_batch_forward(pfft_batch b, const void* in, void* c_hat, void* scaling, void* wavelet,
                                void* stream);
+
+/* PFFT_BATCH_ONE_LAUNCH batches: the number of tries of every dependency
+ * wait before it gives up (also bounded by about one second); spins < 0
+ * restores the default (2^22).  A wait that gives up records
+ * PFFT_ERR_TIMEOUT in the batch's device status word and makes the rest of
+ * the launch return without work (outputs incomplete).  Returns
+ * PFFT_ERR_UNSUPPORTED for other batches.  Takes effect on the next
+ * pfft_batch_forward. */
+pfft_status pfft_batch_set_wait_limit(pfft_batch b, int64_t spins);
+
+/* Reads and clears the batch's device status word on `stream` (synchronising
+ * it): PFFT_OK, or PFFT_ERR_TIMEOUT after a wait of a PFFT_BATCH_ONE_LAUNCH
+ * launch gave up.  PFFT_OK for batches without that flag. */
+pfft_status pfft_batch_device_status(pfft_batch b, void* stream);
 
 pfft_status pfft_batch_destroy(pfft_batch b);
 

@@ -20,8 +20,8 @@ import numpy as np
 import torch
 
 from . import _capi
-from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_BATCH_RADIX8, PFFT_C64, PFFT_C128, PFFT_FLAG_LAYOUT_SNF,
-                    pfft_batch_split_layout,
+from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_BATCH_ONE_LAUNCH, PFFT_BATCH_RADIX8, PFFT_C64, PFFT_C128, PFFT_FLAG_LAYOUT_SNF,
+                    pfft_batch_device_status, pfft_batch_set_wait_limit, pfft_batch_split_layout,
                     PFFT_FLAG_TC_SPLIT,
                     PFFT_MAP_INPUT_BOX,
                     PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_OUTPUT_SNF, PWT_DIRICHLET, PWT_DLVP,
@@ -35,7 +35,8 @@ from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_BATCH_RADIX8,
 
 __all__ = [
     "PatternFFT", "WaveletSplit", "PatternBatch", "pattern_fft", "pattern_ifft", "wavelet_decompose",
-    "PFFT_BATCH_NO_GRAPH", "PFFT_BATCH_AUTOTUNE", "PFFT_BATCH_RADIX8", "PFFT_FLAG_TC_SPLIT", "PFFT_FLAG_LAYOUT_SNF", "PWT_FLAG_INPUT_SNF", "pfft_batch_create", "pfft_batch_info",
+    "PFFT_BATCH_NO_GRAPH", "PFFT_BATCH_AUTOTUNE", "PFFT_BATCH_RADIX8", "PFFT_BATCH_ONE_LAUNCH",
+    "pfft_batch_set_wait_limit", "pfft_batch_device_status", "PFFT_FLAG_TC_SPLIT", "PFFT_FLAG_LAYOUT_SNF", "PWT_FLAG_INPUT_SNF", "pfft_batch_create", "pfft_batch_info",
     "pfft_batch_schedule", "pfft_batch_split_layout", "pfft_batch_forward", "pfft_batch_destroy", "split_general", "merge_general",
     "pwt_split_general", "pwt_merge_general",
     "PfftError", "PFFT_C64", "PFFT_C128", "PWT_DIRICHLET", "PWT_DLVP",
@@ -281,6 +282,14 @@ class PatternBatch:
         pfft_batch_forward(self._h, x.data_ptr(), c_hat.data_ptr(), scaling.data_ptr(), wavelet.data_ptr(),
                            _stream(stream))
         return c_hat, scaling, wavelet
+
+    def set_wait_limit(self, spins: int):
+        """PFFT_BATCH_ONE_LAUNCH batches: tries of every dependency wait (< 0: default)."""
+        pfft_batch_set_wait_limit(self._h, spins)
+
+    def check_device_status(self, stream=None):
+        """Raise PfftError if a wait of the single launch gave up (reads and clears the status)."""
+        pfft_batch_device_status(self._h, _stream(stream))
 
     def close(self):
         if getattr(self, "_h", None):

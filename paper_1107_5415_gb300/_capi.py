@@ -25,7 +25,7 @@ PFFT_FLAG_LAYOUT_SNF = 2
 PFFT_MAP_INPUT_BOX, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_SNF = 0, 1, 2, 3
 PWT_DIRICHLET, PWT_DLVP = 0, 1
 PWT_FLAG_INPUT_SNF = 1
-PFFT_BATCH_NO_GRAPH, PFFT_BATCH_AUTOTUNE, PFFT_BATCH_RADIX8 = 1, 2, 4
+PFFT_BATCH_NO_GRAPH, PFFT_BATCH_AUTOTUNE, PFFT_BATCH_RADIX8, PFFT_BATCH_ONE_LAUNCH = 1, 2, 4, 8
 
 STATUS = {0: "PFFT_OK", 1: "PFFT_ERR_ARG", 2: "PFFT_ERR_SINGULAR", 3: "PFFT_ERR_OVERFLOW",
           4: "PFFT_ERR_NOT_INTEGRAL", 5: "PFFT_ERR_UNSUPPORTED", 6: "PFFT_ERR_OOM", 7: "PFFT_ERR_CUDA",
@@ -60,6 +60,8 @@ _SIGS = {
     "pfft_plan_destroy": (ctypes.c_int, [_vp]),
     "pfft_last_device_status": (ctypes.c_int, [_vp, _vp]),
     "pfft_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "pfft_batch_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "pfft_batch_device_status": (ctypes.c_int, [_vp, _vp]),
     "pfft_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "pfft_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_char_p), _i64p,
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int,
@@ -324,6 +326,16 @@ def pfft_batch_schedule(batch):
 def pfft_batch_forward(batch, in_ptr: int, c_hat_ptr: int, scaling_ptr, wavelet_ptr, stream: int):
     _check(lib().pfft_batch_forward(batch, in_ptr, c_hat_ptr, scaling_ptr, wavelet_ptr, stream),
            "pfft_batch_forward")
+
+
+def pfft_batch_set_wait_limit(batch, spins: int):
+    """Tries of every dependency wait of a single-launch batch (< 0: default)."""
+    _check(lib().pfft_batch_set_wait_limit(batch, int(spins)), "pfft_batch_set_wait_limit")
+
+
+def pfft_batch_device_status(batch, stream: int):
+    """Reads and clears the batch's device status word; raises on PFFT_ERR_TIMEOUT."""
+    _check(lib().pfft_batch_device_status(batch, stream), "pfft_batch_device_status")
 
 
 def pfft_batch_destroy(batch):

@@ -46,6 +46,7 @@ struct pfft_batch_s {
   bool has_split = false;
   std::vector<SplitItem> sitems;   // patterns whose dilation has |det J| = 2
   std::vector<PrimeItem> pitems;   // |det J| = p > 2
+  std::vector<int> split_pat, prime_pat;  // pattern of each split item
   std::vector<int> p;              // |det J_i| (0 without dilations)
   std::vector<int64_t> sc_off, wv_off;
   int64_t sc_total = 0, wv_total = 0;
@@ -59,6 +60,13 @@ struct pfft_batch_s {
   std::vector<cudaEvent_t> events;
   cudaGraphExec_t exec = nullptr;
   const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
+  // single launch (PFFT_BATCH_ONE_LAUNCH): the queue's tables in the schedule
+  // buffer (pointers filled per call), its counters and status word
+  QueueArgs q{};
+  int q_units = 0, q_smem = 0;
+  size_t q_off[14] = {};
+  int* qmem = nullptr;  // [0] status, then the counters of QueueArgs
+  unsigned spin_limit = kSpinLimit;
 
   ~pfft_batch_s() {
     for (auto* P : plans) plan_release(P);
@@ -66,6 +74,7 @@ struct pfft_batch_s {
     for (auto e : events) cudaEventDestroy(e);
     for (auto s : streams) cudaStreamDestroy(s);
     if (cap) cudaStreamDestroy(cap);
+    if (qmem) cudaFree(qmem);
     if (sched) cudaFree(sched);
     if (ws) cudaFree(ws);
   }
@@ -231,6 +240,75 @@ pfft_status build_schedule(pfft_batch_s& B) {
     b.cta0_off = put(c0.data(), c0.size() * sizeof(int));
     pb.push_back(b);
   }
+  // the single-launch queue: rows, columns, p = 2 splits, prime splits, each
+  // list in the buckets' order, with first units, patterns and the patterns'
+  // tile counts
+  if (B.flags & PFFT_BATCH_ONE_LAUNCH) {
+    std::vector<PassArgs> qa;
+    std::vector<int> u0(1, 0), pat, need_r(B.n, 0), need_c(B.n, 0);
+    int smem = 0;
+    auto pass_list = [&](const std::vector<std::vector<Item>>& groups, std::vector<int>& need, size_t* o) {
+      qa.clear();
+      u0.assign(1, 0);
+      pat.clear();
+      for (auto& v : groups)
+        for (auto& it : v) {
+          qa.push_back(it.a);
+          u0.push_back(u0.back() + it.a.groups);
+          pat.push_back(it.pattern);
+          need[it.pattern] += it.a.groups;
+          smem = std::max(smem, it.a.smem_bytes);
+        }
+      o[0] = qa.empty() ? 0 : put(qa.data(), qa.size() * sizeof(PassArgs));
+      o[1] = put(u0.data(), u0.size() * sizeof(int));
+      o[2] = pat.empty() ? 0 : put(pat.data(), pat.size() * sizeof(int));
+      return std::make_pair(int(qa.size()), u0.back());
+    };
+    const auto r = pass_list(rg, need_r, B.q_off + 0);
+    const auto c = pass_list(cg, need_c, B.q_off + 3);
+    B.q.nrow = r.first;
+    B.q.u_rows = r.second;
+    B.q.ncol = c.first;
+    B.q.u_cols = c.second;
+    // split units
+    {
+      std::vector<SplitItem> si;
+      std::vector<int> su0(1, 0), spat;
+      for (int i : sorder) {
+        si.push_back(B.sitems[i]);
+        su0.push_back(su0.back() + int((B.sitems[i].L.mN + kQueueSplitFibres - 1) / kQueueSplitFibres));
+        spat.push_back(B.split_pat[i]);
+      }
+      B.q_off[6] = si.empty() ? 0 : put(si.data(), si.size() * sizeof(SplitItem));
+      B.q_off[7] = put(su0.data(), su0.size() * sizeof(int));
+      B.q_off[8] = spat.empty() ? 0 : put(spat.data(), spat.size() * sizeof(int));
+      B.q.nsplit = int(si.size());
+      B.q.u_splits = su0.back();
+    }
+    {
+      std::vector<int> porder;
+      for (int i = 0; i < int(B.pitems.size()); ++i) porder.push_back(i);
+      auto work = [&](int i) { return (long long)B.pitems[i].P.mN * B.pitems[i].P.nch; };
+      if (B.order == 1) std::stable_sort(porder.begin(), porder.end(), [&](int x, int y) { return work(x) > work(y); });
+      std::vector<PrimeItem> pi;
+      std::vector<int> pu0(1, 0), ppat;
+      for (int i : porder) {
+        pi.push_back(B.pitems[i]);
+        pu0.push_back(pu0.back() + int((work(i) + kMaxThreads - 1) / kMaxThreads));
+        ppat.push_back(B.prime_pat[i]);
+      }
+      B.q_off[9] = pi.empty() ? 0 : put(pi.data(), pi.size() * sizeof(PrimeItem));
+      B.q_off[10] = put(pu0.data(), pu0.size() * sizeof(int));
+      B.q_off[11] = ppat.empty() ? 0 : put(ppat.data(), ppat.size() * sizeof(int));
+      B.q.nprime = int(pi.size());
+      B.q.u_primes = pu0.back();
+    }
+    B.q_off[12] = put(need_r.data(), need_r.size() * sizeof(int));
+    B.q_off[13] = put(need_c.data(), need_c.size() * sizeof(int));
+    B.q.npat = B.n;
+    B.q_smem = smem;
+    B.q_units = B.q.u_rows + B.q.u_cols + B.q.u_splits + B.q.u_primes;
+  }
   void* dev = nullptr;
   if (!host.empty()) {
     if (int e = device_alloc(&dev, host.size())) return pfft_status(e);
@@ -260,6 +338,36 @@ pfft_status enqueue(pfft_batch_s& B, const void* in, void* chat, void* sc, void*
                         cudaMemcpyDeviceToDevice, s) != cudaSuccess)
       return PFFT_ERR_CUDA;
   const char* sched = static_cast<const char*>(B.sched);
+  if (B.flags & PFFT_BATCH_ONE_LAUNCH) {
+    QueueArgs q = B.q;
+    auto at = [&](int i) { return static_cast<const void*>(sched + B.q_off[i]); };
+    q.rows = static_cast<const PassArgs*>(at(0));
+    q.row_u0 = static_cast<const int*>(at(1));
+    q.row_pat = static_cast<const int*>(at(2));
+    q.cols = static_cast<const PassArgs*>(at(3));
+    q.col_u0 = static_cast<const int*>(at(4));
+    q.col_pat = static_cast<const int*>(at(5));
+    q.splits = static_cast<const SplitItem*>(at(6));
+    q.split_u0 = static_cast<const int*>(at(7));
+    q.split_pat = static_cast<const int*>(at(8));
+    q.primes = static_cast<const PrimeItem*>(at(9));
+    q.prime_u0 = static_cast<const int*>(at(10));
+    q.prime_pat = static_cast<const int*>(at(11));
+    q.need_rows = static_cast<const int*>(at(12));
+    q.need_cols = static_cast<const int*>(at(13));
+    q.status = B.qmem;
+    q.counters = B.qmem + 1;
+    q.spin_limit = B.spin_limit;
+    q.base[0] = in;
+    q.base[1] = B.ws;
+    q.base[2] = chat;
+    q.sc = sc;
+    q.wv = wv;
+    if (!(sc && wv)) q.u_splits = q.u_primes = 0;
+    const int units = q.u_rows + q.u_cols + q.u_splits + q.u_primes;
+    if (cudaMemsetAsync(q.counters, 0, sizeof(int) * size_t(2 + 2 * B.n), s) != cudaSuccess) return PFFT_ERR_CUDA;
+    return launch_batch_queue(q, B.dtype, units, B.q_smem, s) == 0 ? PFFT_OK : PFFT_ERR_CUDA;
+  }
   auto phase = [&](const std::vector<Bucket>& bs) -> pfft_status {
     auto launch = [&](const Bucket& b, cudaStream_t st) {
       GroupArgs g;
@@ -412,7 +520,7 @@ pfft_status autotune(pfft_batch_s& B) {
 extern "C" pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, const int64_t* M, const int64_t* J,
                                          int symbol, double eta, int dtype, unsigned flags) {
   if (!out || n < 1 || !d || !M || (dtype != PFFT_C64 && dtype != PFFT_C128) ||
-      (flags & ~unsigned(PFFT_BATCH_NO_GRAPH | PFFT_BATCH_AUTOTUNE | PFFT_BATCH_RADIX8)))
+      (flags & ~unsigned(PFFT_BATCH_NO_GRAPH | PFFT_BATCH_AUTOTUNE | PFFT_BATCH_RADIX8 | PFFT_BATCH_ONE_LAUNCH)))
     return PFFT_ERR_ARG;
   if (J && (symbol != PWT_DIRICHLET && symbol != PWT_DLVP)) return PFFT_ERR_ARG;
   if (J && symbol == PWT_DLVP && !(eta > 0.0 && eta < 1.0)) return PFFT_ERR_ARG;
@@ -431,6 +539,7 @@ extern "C" pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, c
     return st;
   };
   if (prepare_grouped(dtype) != 0) return fail(PFFT_ERR_CUDA);
+  if ((flags & PFFT_BATCH_ONE_LAUNCH) && prepare_queue(dtype) != 0) return fail(PFFT_ERR_CUDA);
   size_t mo = 0;
   bool need_ws = false;
   for (int i = 0; i < n; ++i) {
@@ -483,6 +592,7 @@ extern "C" pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, c
         it.sc_off = B->sc_total;
         it.wv_off = B->wv_total;
         B->sitems.push_back(it);
+        B->split_pat.push_back(i);
       } else {
         if (symbol != PWT_DIRICHLET) return fail(PFFT_ERR_UNSUPPORTED);  // built-in bands: Dirichlet only
         PrimeItem it;
@@ -497,6 +607,7 @@ extern "C" pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, c
         it.sc_off = B->sc_total;
         it.wv_off = B->wv_total;
         B->pitems.push_back(it);
+        B->prime_pat.push_back(i);
       }
       B->p.push_back(int(pdet));
       B->sc_off.push_back(B->sc_total);
@@ -510,6 +621,11 @@ extern "C" pfft_status pfft_batch_create(pfft_batch* out, int n, const int* d, c
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(PFFT_ERR_CUDA);  // tables built
   if (need_ws)
     if (int e = device_alloc(&B->ws, size_t(B->total) * ebytes(dtype))) return fail(pfft_status(e));
+  if (flags & PFFT_BATCH_ONE_LAUNCH) {  // status word and queue counters
+    if (int e = device_alloc(reinterpret_cast<void**>(&B->qmem), sizeof(int) * size_t(3 + 2 * n)))
+      return fail(pfft_status(e));
+    if (cudaMemset(B->qmem, 0, sizeof(int) * size_t(3 + 2 * n)) != cudaSuccess) return fail(PFFT_ERR_CUDA);
+  }
   if (cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(PFFT_ERR_CUDA);
   for (int k = 0; k < kMaxBuckets; ++k) {
     cudaStream_t s;
@@ -573,4 +689,26 @@ extern "C" pfft_status pfft_batch_destroy(pfft_batch b) {
   if (!b) return PFFT_ERR_ARG;
   delete b;
   return PFFT_OK;
+}
+
+extern "C" pfft_status pfft_batch_set_wait_limit(pfft_batch b, int64_t spins) {
+  if (!b) return PFFT_ERR_ARG;
+  if (!(b->flags & PFFT_BATCH_ONE_LAUNCH)) return PFFT_ERR_UNSUPPORTED;
+  b->spin_limit = spins < 0 ? kSpinLimit : unsigned(std::min<int64_t>(spins, int64_t(UINT32_MAX)));
+  if (b->exec) {  // the graph holds the old limit
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pfft_batch_device_status(pfft_batch b, void* stream) {
+  if (!b) return PFFT_ERR_ARG;
+  if (!b->qmem) return PFFT_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int v = 0;
+  if (cudaMemcpyAsync(&v, b->qmem, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemsetAsync(b->qmem, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return PFFT_ERR_CUDA;
+  return pfft_status(v);
 }

@@ -42,6 +42,50 @@ struct alignas(16) PrimeItem {
   long long in_off, sc_off, wv_off;
 };
 
+// The whole batch in one launch (batch_queue_kernel): one queue of work
+// units in dependency order -- every row-pass tile, then every column-pass
+// tile, then the split units -- handed to the CTAs by a counter in the order
+// they start.  A column tile of pattern i starts once all row tiles of
+// pattern i are done, a split unit once the pattern's coefficients are
+// complete; the waits are bounded (spin_limit tries and about one second),
+// after which the kernel records PFFT_ERR_TIMEOUT, raises the abort flag and
+// the CTAs still to run return at once.  Units of the split phases take
+// kQueueSplitFibres fibres (|det J| = 2) or kMaxThreads work items
+// (|det J| > 2).
+constexpr int kQueueSplitFibres = kMaxThreads * kSplitPerThread;
+struct QueueArgs {
+  const PassArgs* rows;          // row-pass items, costliest first
+  const int* row_u0;             // first unit of each row item (prefix, n + 1 entries)
+  const int* row_pat;            // pattern of each row item
+  int nrow;
+  const PassArgs* cols;
+  const int* col_u0;
+  const int* col_pat;
+  int ncol;
+  const SplitItem* splits;
+  const int* split_u0;
+  const int* split_pat;
+  int nsplit;
+  const PrimeItem* primes;
+  const int* prime_u0;
+  const int* prime_pat;
+  int nprime;
+  int u_rows, u_cols, u_splits, u_primes;  // units per phase (split phases 0 without a split)
+  const int* need_rows;  // per pattern: row tiles
+  const int* need_cols;  // per pattern: column tiles (0: the row pass writes the coefficients)
+  int* counters;         // [0] next unit, [1] abort, then rows done [npat], columns done [npat]
+  int npat;
+  int* status;           // device status word (PFFT_ERR_TIMEOUT)
+  unsigned spin_limit;
+  const void* base[3];   // the caller's input, the batch workspace, the caller's output (c_hat)
+  void* sc;
+  void* wv;
+};
+// Raise the shared-memory limit of the queue kernel (once per process; call
+// before any stream capture).
+int prepare_queue(int dtype);
+int launch_batch_queue(const QueueArgs& g, int dtype, int nunits, int smem, cudaStream_t s);
+
 // Raise the dynamic shared-memory limit of the grouped kernels (once per
 // process; call before any stream capture).
 int prepare_grouped(int dtype);

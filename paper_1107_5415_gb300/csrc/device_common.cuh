@@ -19,6 +19,17 @@ struct CT<double> {
   using type = double2;
 };
 
+// Load of data that another CTA of the same launch may have written (COH:
+// through L2, bypassing the non-coherent L1 / read-only paths), or a plain
+// load.
+template <bool COH, typename T>
+__device__ __forceinline__ T load_c(const T* p) {
+  if constexpr (COH)
+    return __ldcg(p);
+  else
+    return *p;
+}
+
 template <typename C>
 __device__ __forceinline__ C cmake(decltype(C::x) a, decltype(C::x) b) {
   C c;

@@ -498,7 +498,7 @@ __device__ __forceinline__ int shear_index(const PassArgs& a, int j, const int* 
 // Column pass: all LB rows of T adjacent workspace columns per CTA, smem
 // layout [i][t].  The DFT runs over the (D-1) cycles inside the pencil.
 // Loads and stores are batched per thread as in the row pass.
-template <typename C, int EPT, bool POW2, bool PAD, bool TCK = true>
+template <typename C, int EPT, bool POW2, bool PAD, bool TCK = true, bool COH = false>
 __device__ __forceinline__ void col_pass_body(const PassArgs& a, int tile, int sig, C* sm) {
   const C* __restrict__ tw = static_cast<const C*>(a.tw);
   const C* __restrict__ in = static_cast<const C*>(a.in) + (int64_t)sig * a.m;
@@ -532,7 +532,7 @@ __device__ __forceinline__ void col_pass_body(const PassArgs& a, int tile, int s
     if (w < n_ok) {
       const int j = a.divT.div(w);
       if (ws_in) {
-        v[k] = __ldg(in + j * a.nD + p0 + tcol);
+        v[k] = COH ? __ldcg(in + j * a.nD + p0 + tcol) : __ldg(in + j * a.nD + p0 + tcol);
         sidx[k] = j * a.T + tcol;
       } else {
         const int i = shear_index(a, j, off);

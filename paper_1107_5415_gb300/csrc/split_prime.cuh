@@ -169,7 +169,7 @@ __device__ __forceinline__ C prime_phase(long long t, long long q) {
 // one signal: coefficients cin / cout (the signal's base), band 0 (the
 // scaling part) at d0 and band j >= 1 at dw + (j - 1) dstride (pointers at
 // fibre gs).  MODE 0: analysis c -> bands; MODE 1: synthesis bands -> c.
-template <typename C, int MODE>
+template <typename C, int MODE, bool COH = false>
 __device__ __forceinline__ void prime_split_item(const PrimeDesc& P, int gs, int j0, const C* __restrict__ cin,
                                                  C* __restrict__ cout, const C* __restrict__ din0,
                                                  const C* __restrict__ dinw, C* __restrict__ dout0,
@@ -202,14 +202,14 @@ __device__ __forceinline__ void prime_split_item(const PrimeDesc& P, int gs, int
   {
     int y[4];
     prime_member(P.HM, g, P.shift, 0, y);
-    C x0 = MODE == 0 ? cin[prime_slot(P.HM, y)] : din0[0];
+    C x0 = MODE == 0 ? load_c<COH>(cin + prime_slot(P.HM, y)) : din0[0];
     sig = x0;  // the e_0 part of V
     for (int i = 0; i < nw; ++i) {
       const int t = tm[i];
       C xt;
       if (MODE == 0) {
         prime_member(P.HM, g, P.shift, t, y);
-        xt = cin[prime_slot(P.HM, y)];
+        xt = load_c<COH>(cin + prime_slot(P.HM, y));
       } else {
         const C dt = t == 0 ? din0[0] : dinw[(long long)(t - 1) * dstride];
         xt = cmul(dt, prime_phase<C>((long long)t * num % P.q, P.q));
@@ -227,7 +227,7 @@ __device__ __forceinline__ void prime_split_item(const PrimeDesc& P, int gs, int
     const int sl = prime_slot(P.HM, y);
     const C e = prime_phase<C>((long long)j * num % P.q, P.q);
     if (MODE == 0) {
-      const C xj = csub(cscale(sig, coef * vj), cin[sl]);
+      const C xj = csub(cscale(sig, coef * vj), load_c<COH>(cin + sl));
       (j == 0 ? dout0 : doutw + (long long)(j - 1) * dstride)[0] = cmul(cconj(e), xj);
     } else {
       const C yj = cmul((j == 0 ? din0 : dinw + (long long)(j - 1) * dstride)[0], e);

@@ -142,7 +142,7 @@ __device__ __forceinline__ C wavelet_phase(const LevelDesc& L, const int* h) {
 // fibre of slot gs of the box of H(N^T) in each of `batch` signals (signal b
 // at c + b mM, d + b mN).  The symbols depend on the fibre only: they are
 // evaluated once and applied to every signal.
-template <typename C, int MODE, bool TAB, bool SMALL>
+template <typename C, int MODE, bool TAB, bool SMALL, bool COH = false>
 __device__ __forceinline__ void split_fibre(const LevelDesc& L, int gs, int batch, const C* __restrict__ cin,
                                             C* __restrict__ cout, const C* __restrict__ d1in,
                                             const C* __restrict__ d2in, C* __restrict__ d1out,
@@ -202,7 +202,7 @@ __device__ __forceinline__ void split_fibre(const LevelDesc& L, int gs, int batc
     const C ce = cconj(e0);
 #pragma unroll 4
     for (int b = 0; b < batch; ++b) {
-      const C c0 = cin[b * mM + slot0], c1 = cin[b * mM + slot1];
+      const C c0 = load_c<COH>(cin + b * mM + slot0), c1 = load_c<COH>(cin + b * mM + slot1);
       d1out[b * mN + gs] = cscale(cadd(cscale(c0, A0), cscale(c1, A1)), r2);
       // conj(B0) c0 + conj(B1) c1 = conj(e0) (A1 c0 - A0 c1)
       d2out[b * mN + gs] = cscale(cmul(ce, csub(cscale(c0, A1), cscale(c1, A0))), r2);
