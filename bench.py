@@ -529,6 +529,25 @@ def bench_mix(pf, torch, peaks_hbm, steps=10, warmup=3, n_patterns=None):
         out[name] = {"value": B.total / (ms * 1e-3), "unit": "points/s", "ms": ms,
                      "compulsory_gbs": alg / (ms * 1e-3) / 1e9, "compulsory_frac": alg / (ms * 1e-3) / 1e9 / peaks_hbm}
     B.close()
+    # the same batch in one launch (device work queue, bounded dependency waits)
+    t0 = time.perf_counter()
+    Q = pf.PatternBatch(Ms, Js, pf.PWT_DIRICHLET, flags=pf.PFFT_BATCH_AUTOTUNE | pf.PFFT_BATCH_ONE_LAUNCH)
+    out["one_launch_plan_s"] = time.perf_counter() - t0
+    for split, name in ((True, "fft_split_one_launch"), (False, "fft_only_one_launch")):
+        for _ in range(warmup):
+            Q.forward(x, chat, sc, wv, split=split)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            Q.forward(x, chat, sc, wv, split=split)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"value": Q.total / (ms * 1e-3), "unit": "points/s", "ms": ms, "launches_per_step": 1}
+    Q.check_device_status()
+    Q.close()
     return out
 
 
