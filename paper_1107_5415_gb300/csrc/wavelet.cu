@@ -392,10 +392,7 @@ static pfft_status plan_device(pwt_plan_s& P) {
       float4* t = static_cast<float4*>(P.symtab);
       for (auto& L : P.lv) {
         if (!L.small) continue;
-        L.symtab = t;
-        const int grd = int(std::min<long long>((L.mN + 255) / 256, 152LL * 8));
-        symbol_table_kernel<float2><<<grd, 256>>>(L, t);
-        if (cudaGetLastError() != cudaSuccess) return PFFT_ERR_CUDA;
+        if (launch_symbol_table(L, t) != 0) return PFFT_ERR_CUDA;
         t += L.mN;
       }
     }
@@ -564,6 +561,15 @@ extern "C" pfft_status pwt_adjoint(pwt_plan p, const void* scaling, const void* 
 // legacy stream.
 size_t pfft::split_table_elems(const LevelDesc& L) {
   return size_t(1 << kLoBits) + size_t((L.q + (1LL << kLoBits) - 1) >> kLoBits);
+}
+
+int pfft::launch_symbol_table(LevelDesc& L, void* tab) {
+  if (!L.small || !L.tab_lo) return -1;
+  const int grd = int(std::min<long long>((L.mN + 255) / 256, 152LL * 8));
+  symbol_table_kernel<float2><<<grd, 256>>>(L, static_cast<float4*>(tab));
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  L.symtab = tab;
+  return 0;
 }
 
 int pfft::launch_split_tables(LevelDesc& L, void* tab, int dtype) {

@@ -184,18 +184,31 @@ __device__ __forceinline__ void split_fibre(const LevelDesc& L, int gs, int batc
       slot1 += mu1 * L.snf_str[j];
     }
   }
-  const Rl w0 = fibre_weight<Rl, SMALL>(L, g);
-  const Rl w1 = Rl(1) - w0;
   Rl A0, A1;
-  if (L.symbol == PWT_DIRICHLET) {
-    A0 = sqrt(Rl(2) * w0);
-    A1 = sqrt(Rl(2) * w1);
-  } else {
-    A0 = Rl(1.41421356237309504880) * w0;
-    A1 = Rl(1.41421356237309504880) * w1;
+  C e0;
+  bool tabulated = false;
+  if constexpr (sizeof(Rl) == 4) {
+    if (L.symtab) {  // the plan's per-fibre symbols: A(h0), A(h1), conj(e(h0))
+      const float4 t = __ldg(static_cast<const float4*>(L.symtab) + gs);
+      A0 = t.x;
+      A1 = t.y;
+      e0 = cmake<C>(t.z, -t.w);
+      tabulated = true;
+    }
+  }
+  if (!tabulated) {
+    const Rl w0 = fibre_weight<Rl, SMALL>(L, g);
+    const Rl w1 = Rl(1) - w0;
+    if (L.symbol == PWT_DIRICHLET) {
+      A0 = sqrt(Rl(2) * w0);
+      A1 = sqrt(Rl(2) * w1);
+    } else {
+      A0 = Rl(1.41421356237309504880) * w0;
+      A1 = Rl(1.41421356237309504880) * w1;
+    }
+    e0 = wavelet_phase<C, TAB, SMALL>(L, g);
   }
   // B(h0) = A(h1) e(h0), B(h1) = A(h0) e(h1), e(h1) = -e(h0)
-  const C e0 = wavelet_phase<C, TAB, SMALL>(L, g);
   const Rl r2 = Rl(0.70710678118654752440);
   const long long mM = L.mM, mN = L.mN;
   if (MODE == 0) {
@@ -459,6 +472,10 @@ inline void split_grid(long long mN, int batch, unsigned& gx, unsigned& gy, int&
 // construction at `tab` (sets tab_lo / tab_hi; 0 on success).
 size_t split_table_elems(const LevelDesc& L);
 int launch_split_tables(LevelDesc& L, void* tab, int dtype);
+// The per-fibre symbol table of a complex64 level with the int32 index path
+// (L.small, phase tables built): L.mN float4 at `tab`, set as L.symtab
+// (0 on success).
+int launch_symbol_table(LevelDesc& L, void* tab);
 
 // Host: the descriptor of one split level of M by J (wavelet.cu).
 pfft_status describe_split_level(int d, const int64_t* M, const int64_t* J, int symbol, double eta,
