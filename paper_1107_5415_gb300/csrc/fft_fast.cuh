@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "fft_plan.hpp"
+#include "fft_tc.cuh"
 
 namespace pfft {
 
@@ -115,9 +116,11 @@ __device__ __forceinline__ void main_twiddle(C* v, const C* stw) {
 
 // All stages of one pencil on the thread's registers v[R].  On entry v holds
 // elements p + P k; on exit v holds output frequencies p + P k.
-template <typename C, int R, bool COLS>
+// TC (complex64, radix 32): the main stages' butterflies on the tensor cores
+// (fft_tc.cuh, tc_dft32_regs); the tail stage stays in registers.
+template <typename C, int R, bool COLS, bool TC = false>
 __device__ __forceinline__ void fast_pencil_dft(C* v, C* sm, const C* stw, const PassArgs& a, int p,
-                                                int pencil_base, int escale, int L) {
+                                                int pencil_base, int escale, int L, TcRegs* tcx = nullptr) {
   const int P = L / R;
   int Ns = 1;
   bool in_regs = true;
@@ -142,7 +145,12 @@ __device__ __forceinline__ void fast_pencil_dft(C* v, C* sm, const C* stw, const
     const int k = p & (Ns - 1);
     constexpr int NB = (R == 32) ? 5 : 4;
     if (k) main_twiddle<C, R>(v, stw + a.stw_off[s] + k * NB);
-    dft_pow2<C, R>(v);
+    if constexpr (TC) {
+      if (in_regs) __syncthreads();  // the tile may hold the input gather's staging
+      tc_dft32_regs(v, *tcx, a);
+    } else {
+      dft_pow2<C, R>(v);
+    }
     if (s + 1 < a.fast_nmain) {
       const int ob = (p - k) * R + k;
 #pragma unroll
@@ -198,12 +206,14 @@ __device__ __forceinline__ void gather_point(const PassArgs& a, int e, int* bt) 
 
 // Row pass, power-of-two nD.  Thread (t, p): pencil (row) t, elements
 // p + P k.  Consecutive threads hold consecutive elements of a row.
-template <typename C, int R, int DIM>
+template <typename C, int R, int DIM, bool TC = false>
 __global__ void __launch_bounds__(kMaxThreads, 1) row_fast_kernel(PassArgs a) {
   constexpr int TS = DIM <= 2 ? 2 : 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   C* stw = stage_table(sm, a);
+  TcRegs tcx;
+  if constexpr (TC) tc_regs_begin(tcx, smem_raw, a.tc_off, reinterpret_cast<const float2*>(a.tw), a.tw_n);
   const C* __restrict__ in = static_cast<const C*>(a.in) + (int64_t)blockIdx.y * a.m;
   C* __restrict__ out = static_cast<C*>(a.out) + (int64_t)blockIdx.y * a.m;
   const int L = a.L;
@@ -244,7 +254,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_fast_kernel(PassArgs a) {
   }
   cp_async_wait_all();
   __syncthreads();
-  fast_pencil_dft<C, R, false>(v, sm, stw, a, p, t * L, 1, L);
+  fast_pencil_dft<C, R, false, TC>(v, sm, stw, a, p, t * L, 1, L, &tcx);
+  if constexpr (TC) tc_regs_end(tcx);
   if (!live) return;
   using Rl = decltype(C::x);
   const Rl sc = Rl(a.scale);
@@ -281,12 +292,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1) row_fast_kernel(PassArgs a) {
 // length LB, a power of two).  Thread (t, p), t fastest: column p0 + t, rows
 // p + P k.  Workspace loads are coalesced in t; the sheared box store (or
 // load, inverse) goes through shared memory in the walk of fft_kernels.cuh.
-template <typename C, int R, int DIM>
+template <typename C, int R, int DIM, bool TC = false>
 __global__ void __launch_bounds__(kMaxThreads, 1) col_fast_kernel(PassArgs a) {
   constexpr int TS = DIM <= 2 ? 2 : 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   C* stw = stage_table(sm, a);
+  TcRegs tcx;
+  if constexpr (TC) tc_regs_begin(tcx, smem_raw, a.tc_off, reinterpret_cast<const float2*>(a.tw), a.tw_n);
   const C* __restrict__ in = static_cast<const C*>(a.in) + (int64_t)blockIdx.y * a.m;
   C* __restrict__ out = static_cast<C*>(a.out) + (int64_t)blockIdx.y * a.m;
   const int T = a.T;
@@ -327,7 +340,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) col_fast_kernel(PassArgs a) {
     for (int k = 0; k < R; ++k) v[k] = sm[fphys((p + P * k) * T + tcol)];
     __syncthreads();
   }
-  fast_pencil_dft<C, R, true>(v, sm, stw, a, p, tcol, T, a.L);
+  fast_pencil_dft<C, R, true, TC>(v, sm, stw, a, p, tcol, T, a.L, &tcx);
+  if constexpr (TC) tc_regs_end(tcx);
   using Rl = decltype(C::x);
   const Rl sc = Rl(a.scale);
   if (a.store_mode == MAP_WS) {

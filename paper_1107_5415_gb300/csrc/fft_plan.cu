@@ -167,7 +167,7 @@ bool set_stages(PassArgs& p, std::vector<StageDesc> all) {
     if (reg < 0) return false;
     p.st[i] = all[i];
     p.cnt[reg] += 1;
-    if (reg > 3) p.pow2 = 0;
+    if (reg > 3 && reg != kTC32Region) p.pow2 = 0;  // radix 32 (tensor-core plans) is a power of two
   }
   return true;
 }
@@ -246,7 +246,10 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
     const int Rm = P.dtype == PFFT_C64 ? 32 : 16;
     const int L = p.L;
     const bool pow2L = L >= Rm && (L & (L - 1)) == 0 && (T & (T - 1)) == 0;
-    p.fast = (!P.generic_only && p.tw_n == P.nD && p.pow2 && pow2L && P.d <= 3 && (!cols || P.pen.size() == 1) && T * L <= (P.dtype == PFFT_C64 ? 16384 : 8192)) ? 1 : 0;
+    // split-precision plans use them too, their radix-32 main stages on the tensor cores
+    const bool tc_fast = P.tc && P.dtype == PFFT_C64 && p.tw_n % 32 == 0;
+    // (a column tile of the register-resident pass holds T whole columns: T divides nD)
+    p.fast = ((!P.generic_only || tc_fast) && p.tw_n == P.nD && p.pow2 && pow2L && P.d <= 3 && (!cols || P.pen.size() == 1) && (!cols || P.nD % T == 0) && T * L <= (P.dtype == PFFT_C64 ? 16384 : 8192)) ? 1 : 0;
     if (p.fast) {
       int lg = 0, lr = 0;
       while ((1 << lg) < L) ++lg;
@@ -265,8 +268,16 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
       const int nel = T * L;
       p.stw_smem_off = (nel + (nel >> 5) + 1) & ~1;
       p.smem_bytes = int(size_t(p.stw_smem_off + p.stw_n) * elem_bytes(P.dtype));
-      if (p.nthreads <= kMaxThreads && p.smem_bytes <= 227 * 1024 && p.fast_nmain <= 4) return PFFT_OK;
+      bool ok = true;
+      if (P.tc) {  // W (radix 32), mbarrier and tensor-memory address after the stage table (fft_tc.cuh)
+        p.tc = 1;
+        p.tc_off = (p.smem_bytes + 15) & ~15;
+        p.smem_bytes = p.tc_off + tc_regs_extra_bytes();
+        ok = p.nthreads % 128 == 0 && p.fast_nmain >= 1;
+      }
+      if (ok && p.nthreads <= kMaxThreads && p.smem_bytes <= 227 * 1024 && p.fast_nmain <= 4) return PFFT_OK;
       p.fast = 0;
+      p.tc = 0;
     }
   }
   // generic kernels: 16 points per thread (64 registers, two CTAs per SM)
@@ -693,7 +704,7 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
     while (idx.size() - base.back() < size_t(p->stw_n)) idx.push_back(0);
   }
   // runs of consecutive box slots along each row, for bulk-copy staging
-  if (P.rowp.fast && P.rowp.T == 1 && npen >= 1 && (P.m * elem_bytes(P.dtype)) % 16 == 0) {
+  if (P.rowp.fast && !P.tc && P.rowp.T == 1 && npen >= 1 && (P.m * elem_bytes(P.dtype)) % 16 == 0) {
     std::vector<std::array<int, 4>> runs;
     int maxr = 0;
     bool ok = true;
@@ -788,7 +799,7 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
     }
   }
   // pencils of 2^10 complex64 points, 8 per tile: the persistent pipelined column pass
-  if (npen == 1 && P.dtype == PFFT_C64 && P.colp.fast && P.colp.L == (1 << kCPipeLogL) && P.colp.T == 8 &&
+  if (npen == 1 && P.dtype == PFFT_C64 && !P.tc && P.colp.fast && P.colp.L == (1 << kCPipeLogL) && P.colp.T == 8 &&
       P.colp.LB == P.colp.L && P.colp.nthreads == 256 && P.colp.fast_tail == 1 && P.colp.fast_nmain == 2 &&
       (d == 2 || d == 3) && P.nD % 8 == 0) {
     int nsm = 0;

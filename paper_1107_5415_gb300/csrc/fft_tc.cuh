@@ -41,6 +41,10 @@
 
 namespace pfft {
 
+// Shared-memory tile index of the generic passes (fft_kernels.cuh).
+template <bool PAD>
+__device__ __forceinline__ int phys(int x);
+
 // Byte offset of element (row, k) of a K-major fp16 operand with K columns:
 // core matrices of 8 rows x 16 bytes, the core matrices of one 8-row group
 // adjacent along K (128 bytes apart), 8-row groups K x 16 bytes apart.
@@ -97,7 +101,6 @@ __host__ __device__ inline int tc_tmem_cols(int points, bool has32, bool has16) 
   return c;
 }
 
-#if defined(__CUDA_ARCH__)
 __device__ __forceinline__ uint32_t tc_smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -350,6 +353,151 @@ __device__ __noinline__ void run_tc_stage(float2* sm, const PassArgs& a, const S
   tc_fence_before();
   __syncthreads();
 }
-#endif  // __CUDA_ARCH__
+// ---- The same product inside the register-resident passes (fft_fast.cuh):
+// every thread holds one radix-32 butterfly in registers, so it scales,
+// splits and stages its own row of A (row = thread index, over the tile,
+// whose reads are complete), and reads its own row of D back (warp w reads
+// lanes 32 (w mod 4) .. of chunk w / 4: rows 32 w .. 32 w + 31, i.e. its own
+// threads).  The block size is a multiple of 128.
+struct TcRegs {
+  unsigned char* stg;  // the tile (staging)
+  uint32_t w32;        // shared address of W (hi, lo), radix 32
+  uint32_t bar;        // shared address of the mbarrier
+  uint32_t tmem;       // tensor-memory base
+  uint32_t phase;
+  int ok;
+};
 
+// Shared-memory bytes the register-resident passes add for the tensor cores
+// (after their own footprint): W of radix 32 (hi, lo), the mbarrier and the
+// tensor-memory address.
+__host__ __device__ constexpr int tc_regs_extra_bytes() { return tc_w_bytes(32) + 16; }
+
+// Set-up at the start of a register-resident pass (all threads): W, the
+// mbarrier, the tensor memory (one 64-column accumulator per 128 threads).
+__device__ __forceinline__ void tc_regs_begin(TcRegs& cx, unsigned char* smem, int tc_off, const float2* tw,
+                                              int tw_n) {
+  unsigned char* w = smem + tc_off;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(w + tc_w_bytes(32) + 8);
+  tc_build_w<32>(w, tw, tw_n);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc_smem_u32(w + tc_w_bytes(32))) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  const int cols = tc_tmem_cols(int(blockDim.x) * 32, true, false);
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc_smem_u32(tslot)),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  cx.stg = smem;
+  cx.w32 = tc_smem_u32(w);
+  cx.bar = tc_smem_u32(w + tc_w_bytes(32));
+  cx.tmem = *tslot;
+  cx.phase = 0;
+  cx.ok = 1;
+}
+
+__device__ __forceinline__ void tc_regs_end(const TcRegs& cx) {
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    const int cols = tc_tmem_cols(int(blockDim.x) * 32, true, false);
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(cx.tmem), "r"(cols) : "memory");
+  }
+}
+
+// v[r] <- sum_s omega_32^{r s} v[s] for the thread's butterfly, on the tensor
+// cores.  Entry: every thread's reads of the tile are complete (a barrier
+// separates them from this call).  Exit: the tile is free again.
+__device__ __forceinline__ void tc_dft32_regs(float2* v, TcRegs& cx, const PassArgs& a) {
+  constexpr int R = 32, K = 64;
+  constexpr int CHB = tc_chunk_bytes(R);
+  float mx = 0.f;
+#pragma unroll
+  for (int r = 0; r < R; ++r) mx = fmaxf(mx, fmaxf(fabsf(v[r].x), fabsf(v[r].y)));
+  int e = mx > 0.f ? 10 - ilogbf(mx) : 0;
+  e = e > 126 ? 126 : (e < -126 ? -126 : e);
+  const float up = __int_as_float((127 + e) << 23);
+  {
+    unsigned char* ch = cx.stg + (threadIdx.x >> 7) * CHB;
+    const int m = threadIdx.x & 127;
+#pragma unroll
+    for (int kg = 0; kg < K / 8; ++kg) {
+      // inputs 8 kg .. 8 kg + 7 of [Re x; Im x]
+      float f[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int kk = 8 * kg + i;
+        f[i] = (kk < R ? v[kk].x : v[kk - R].y) * up;
+      }
+      uint4 h, l;
+      split_h2(f[0], f[1], h.x, l.x);
+      split_h2(f[2], f[3], h.y, l.y);
+      split_h2(f[4], f[5], h.z, l.z);
+      split_h2(f[6], f[7], h.w, l.w);
+      const uint32_t off = tc_kmajor_off(m, 8 * kg, K);
+      *reinterpret_cast<uint4*>(ch + off) = h;
+      *reinterpret_cast<uint4*>(ch + tc_half_bytes(128, K) + off) = l;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  __syncthreads();
+  const int nch = int(blockDim.x) >> 7;
+  if (threadIdx.x == 0 && cx.ok) {
+    tc_fence_after();
+    constexpr uint32_t idesc = tc_instr_desc(128, K);
+    const uint32_t sb = tc_smem_u32(cx.stg);
+    for (int c = 0; c < nch; ++c) {
+      const uint32_t ahi = sb + c * CHB, alo = ahi + tc_half_bytes(128, K);
+      const uint32_t dt = cx.tmem + uint32_t(c * K);
+#pragma unroll
+      for (int kk = 0; kk < K / 16; ++kk) {
+        const uint64_t dah = tc_smem_desc(ahi + kk * 256, 128, K * 16);
+        const uint64_t dal = tc_smem_desc(alo + kk * 256, 128, K * 16);
+        const uint64_t dbh = tc_smem_desc(cx.w32 + kk * 256, 128, K * 16);
+        const uint64_t dbl = tc_smem_desc(cx.w32 + tc_half_bytes(K, K) + kk * 256, 128, K * 16);
+        tc_mma(dt, dah, dbh, idesc, kk > 0 ? 1u : 0u);
+        tc_mma(dt, dah, dbl, idesc, 1u);
+        tc_mma(dt, dal, dbh, idesc, 1u);
+      }
+    }
+    tc_commit(cx.bar);
+  }
+  bool done = cx.ok != 0;
+  if (done) {
+    done = tc_mbar_wait_bounded(cx.bar, cx.phase, a.spin_limit);
+    if (!done) {
+      if (threadIdx.x == 0) atomicExch(a.status, 8);  // PFFT_ERR_TIMEOUT
+      tc_mbar_wait_bounded(cx.bar, cx.phase, kSpinLimit);
+    }
+    cx.phase ^= 1u;
+  }
+  done = __syncthreads_and(done ? 1 : 0) != 0;
+  if (!done) cx.ok = 0;
+  tc_fence_after();
+  {
+    const int warp = threadIdx.x >> 5;
+    const uint32_t ta = cx.tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t((warp >> 2) * K);
+    const float down = __int_as_float((127 - e) << 23);
+#pragma unroll
+    for (int h = 0; h < R / 16; ++h) {
+      uint32_t re[16], im[16];
+      tc_ld16(ta + 16 * h, re);
+      tc_ld16(ta + R + 16 * h, im);
+      tc_wait_ld();
+#pragma unroll
+      for (int so = 0; so < 16; ++so)
+        v[16 * h + so] = make_float2(__uint_as_float(re[so]) * down, __uint_as_float(im[so]) * down);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+}
 }  // namespace pfft
