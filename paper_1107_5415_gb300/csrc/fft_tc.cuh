@@ -155,11 +155,11 @@ __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sy
 
 // Two fp32 values -> packed fp16 pairs (hi, lo); the first value in the low half.
 __device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
-  const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
-  const __half l0 = __float2half_rn(x0 - __half2float(h0));
-  const __half l1 = __float2half_rn(x1 - __half2float(h1));
-  hi = uint32_t(__half_as_ushort(h0)) | (uint32_t(__half_as_ushort(h1)) << 16);
-  lo = uint32_t(__half_as_ushort(l0)) | (uint32_t(__half_as_ushort(l1)) << 16);
+  const __half2 h = __floats2half2_rn(x0, x1);  // packed conversions, round to nearest
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 // W of radix R, hi and lo, as the K-major operand B (row n = output n of
@@ -358,30 +358,36 @@ __device__ __noinline__ void run_tc_stage(float2* sm, const PassArgs& a, const S
 // splits and stages its own row of A (row = thread index, over the tile,
 // whose reads are complete), and reads its own row of D back (warp w reads
 // lanes 32 (w mod 4) .. of chunk w / 4: rows 32 w .. 32 w + 31, i.e. its own
-// threads).  The block size is a multiple of 128.
+// threads).  The block size is a multiple of 128.  Each 128-thread chunk
+// runs on its own: its four warps stage their rows and meet at a named
+// barrier, one of them issues the chunk's MMAs and commits them to the
+// chunk's mbarrier, and the four warps wait for that one only, so the
+// products of one chunk overlap the staging of the others.
+constexpr int kTcMaxChunks = 4;  // 512 threads
 struct TcRegs {
   unsigned char* stg;  // the tile (staging)
   uint32_t w32;        // shared address of W (hi, lo), radix 32
-  uint32_t bar;        // shared address of the mbarrier
+  uint32_t bar;        // shared address of the chunks' mbarriers (8 bytes each)
   uint32_t tmem;       // tensor-memory base
   uint32_t phase;
   int ok;
 };
 
 // Shared-memory bytes the register-resident passes add for the tensor cores
-// (after their own footprint): W of radix 32 (hi, lo), the mbarrier and the
-// tensor-memory address.
-__host__ __device__ constexpr int tc_regs_extra_bytes() { return tc_w_bytes(32) + 16; }
+// (after their own footprint): W of radix 32 (hi, lo), the chunks' mbarriers
+// and the tensor-memory address.
+__host__ __device__ constexpr int tc_regs_extra_bytes() { return tc_w_bytes(32) + 8 * kTcMaxChunks + 16; }
 
 // Set-up at the start of a register-resident pass (all threads): W, the
 // mbarrier, the tensor memory (one 64-column accumulator per 128 threads).
 __device__ __forceinline__ void tc_regs_begin(TcRegs& cx, unsigned char* smem, int tc_off, const float2* tw,
                                               int tw_n) {
   unsigned char* w = smem + tc_off;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(w + tc_w_bytes(32) + 8);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(w + tc_w_bytes(32) + 8 * kTcMaxChunks);
   tc_build_w<32>(w, tw, tw_n);
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc_smem_u32(w + tc_w_bytes(32))) : "memory");
+  if (threadIdx.x < kTcMaxChunks) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc_smem_u32(w + tc_w_bytes(32) + 8 * threadIdx.x))
+                 : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   const int cols = tc_tmem_cols(int(blockDim.x) * 32, true, false);
@@ -448,39 +454,34 @@ __device__ __forceinline__ void tc_dft32_regs(float2* v, TcRegs& cx, const PassA
     }
   }
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-  __syncthreads();
-  const int nch = int(blockDim.x) >> 7;
-  if (threadIdx.x == 0 && cx.ok) {
+  const int c = threadIdx.x >> 7;
+  asm volatile("bar.sync %0, 128;\n" ::"r"(1 + c) : "memory");  // the chunk's rows are staged
+  const uint32_t bar = cx.bar + 8 * c;
+  if ((threadIdx.x & 127) == 0 && cx.ok) {
     tc_fence_after();
     constexpr uint32_t idesc = tc_instr_desc(128, K);
-    const uint32_t sb = tc_smem_u32(cx.stg);
-    for (int c = 0; c < nch; ++c) {
-      const uint32_t ahi = sb + c * CHB, alo = ahi + tc_half_bytes(128, K);
-      const uint32_t dt = cx.tmem + uint32_t(c * K);
+    const uint32_t ahi = tc_smem_u32(cx.stg) + c * CHB, alo = ahi + tc_half_bytes(128, K);
+    const uint32_t dt = cx.tmem + uint32_t(c * K);
 #pragma unroll
-      for (int kk = 0; kk < K / 16; ++kk) {
-        const uint64_t dah = tc_smem_desc(ahi + kk * 256, 128, K * 16);
-        const uint64_t dal = tc_smem_desc(alo + kk * 256, 128, K * 16);
-        const uint64_t dbh = tc_smem_desc(cx.w32 + kk * 256, 128, K * 16);
-        const uint64_t dbl = tc_smem_desc(cx.w32 + tc_half_bytes(K, K) + kk * 256, 128, K * 16);
-        tc_mma(dt, dah, dbh, idesc, kk > 0 ? 1u : 0u);
-        tc_mma(dt, dah, dbl, idesc, 1u);
-        tc_mma(dt, dal, dbh, idesc, 1u);
-      }
+    for (int kk = 0; kk < K / 16; ++kk) {
+      const uint64_t dah = tc_smem_desc(ahi + kk * 256, 128, K * 16);
+      const uint64_t dal = tc_smem_desc(alo + kk * 256, 128, K * 16);
+      const uint64_t dbh = tc_smem_desc(cx.w32 + kk * 256, 128, K * 16);
+      const uint64_t dbl = tc_smem_desc(cx.w32 + tc_half_bytes(K, K) + kk * 256, 128, K * 16);
+      tc_mma(dt, dah, dbh, idesc, kk > 0 ? 1u : 0u);
+      tc_mma(dt, dah, dbl, idesc, 1u);
+      tc_mma(dt, dal, dbh, idesc, 1u);
     }
-    tc_commit(cx.bar);
+    tc_commit(bar);
   }
   bool done = cx.ok != 0;
   if (done) {
-    done = tc_mbar_wait_bounded(cx.bar, cx.phase, a.spin_limit);
+    done = tc_mbar_wait_bounded(bar, cx.phase, a.spin_limit);
     if (!done) {
-      if (threadIdx.x == 0) atomicExch(a.status, 8);  // PFFT_ERR_TIMEOUT
-      tc_mbar_wait_bounded(cx.bar, cx.phase, kSpinLimit);
+      if ((threadIdx.x & 127) == 0) atomicExch(a.status, 8);  // PFFT_ERR_TIMEOUT
+      tc_mbar_wait_bounded(bar, cx.phase, kSpinLimit);
     }
-    cx.phase ^= 1u;
   }
-  done = __syncthreads_and(done ? 1 : 0) != 0;
-  if (!done) cx.ok = 0;
   tc_fence_after();
   {
     const int warp = threadIdx.x >> 5;
@@ -498,6 +499,7 @@ __device__ __forceinline__ void tc_dft32_regs(float2* v, TcRegs& cx, const PassA
     }
   }
   tc_fence_before();
-  __syncthreads();
+  if (cx.ok) cx.phase ^= 1u;
+  if (!__syncthreads_and(done ? 1 : 0)) cx.ok = 0;  // every chunk's products are complete
 }
 }  // namespace pfft
