@@ -338,8 +338,8 @@ def bench_step5(pf, torch, steps=20, warmup=3):
 
 def bench_tc(pf, torch, x, y_fp32, ms_fp32, peaks_hbm, steps=50, warmup=5):
     """The same step (forward + inverse of the batched 2-D workload) in the
-    split-precision tensor-core form: radix-16 / 32 stages as fp16 hi + lo
-    DFT-matrix products on the tensor cores with fp32 accumulation.  Reports
+    split-precision tensor-core form: the radix-32 stages as fp16 hi + lo
+    DFT-matrix products on the tensor cores (tcgen05) with fp32 accumulation.  Reports
     its speed against the plain fp32 form measured above and its agreement
     with it (the error against the FP64 oracle is checked by the tests)."""
     w = SI.WORKLOADS[WORKLOAD]
@@ -370,7 +370,7 @@ def bench_tc(pf, torch, x, y_fp32, ms_fp32, peaks_hbm, steps=50, warmup=5):
     kernels = {k: {"launches": int(v[0]), "avg_ms": v[1] / max(v[0], 1),
                    "achieved_gbs": BYTES_PER_POINT_PASS * x.numel() / (v[1] / max(v[0], 1) * 1e-3) / 1e9}
                for k, v in prof.items() if v[0]}
-    return {"form": "split fp16 (hi + lo) tensor-core radix-16/32 stages, fp32 accumulation",
+    return {"form": "split fp16 (hi + lo) radix-32 stages on tcgen05 (radix-16 tail in fp32), fp32 accumulation",
             "value": pts / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
             "speedup_vs_plain_fp32": ms_fp32 / ms, "rel_l2_vs_plain_fp32": num / den,
             "round_trip_rel_l2": rt, "kernels": kernels,

@@ -80,10 +80,13 @@ enum { PFFT_C64 = 0, PFFT_C128 = 1 };
 
 /* Flags of pfft_plan_create. */
 enum {
-  /* Split-precision tensor-core form (PFFT_C64 only): the radix-16 and
-   * radix-32 stages run as dense DFT-matrix products on the tensor cores in
-   * fp16 with fp32 accumulation, each operand split into hi + lo fp16 halves
-   * (three products per tile), which recovers fp32-level accuracy.  Each
+  /* Split-precision tensor-core form (PFFT_C64 only): the radix-32 stages
+   * (and, in passes that do not fit the register-resident kernels, the
+   * radix-16 stages) run as dense DFT-matrix products on the tensor cores
+   * (tcgen05, fp16 operands, fp32 accumulation in tensor memory), each
+   * operand split into hi + lo fp16 halves (three products per K step),
+   * which recovers fp32-level accuracy.  The form uses neither the bulk-copy
+   * nor the pipelined passes.  Each
    * butterfly is scaled by a power of two before the split and back after
    * the product (exact), so the accuracy holds for data of any magnitude
    * within the fp32 range.  Without the flag every stage runs in plain fp32
