@@ -267,7 +267,15 @@ def bench_wavelet(pf, torch, peaks_hbm, steps=20, warmup=3):
             ms = e0.elapsed_time(e1) / steps
             pts = plan.sizes[0] * batch
             if L == levels:
-                out[name] = {"value": pts / (ms * 1e-3), "unit": "points/s", "ms": ms}
+                # compulsory bytes of the fused cascade: each group of three levels reads its
+                # input once and writes every part once (16 B per input point of the group)
+                alg, n_in = 0, pts
+                for _ in range(0, levels, 3):
+                    alg += 16 * n_in
+                    n_in //= 8
+                out[name] = {"value": pts / (ms * 1e-3), "unit": "points/s", "ms": ms,
+                             "cascade_alg_bytes": alg, "cascade_gbs": alg / (ms * 1e-3) / 1e9,
+                             "cascade_frac": alg / (ms * 1e-3) / 1e9 / peaks_hbm}
             else:
                 gbs = 16 * pts / (ms * 1e-3) / 1e9
                 out[name]["level1_kernel"] = {"avg_ms": ms, "achieved_gbs": gbs, "frac": gbs / peaks_hbm,
