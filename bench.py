@@ -416,7 +416,10 @@ def bench_table1(pf, torch, peaks_hbm, steps=20, warmup=3):
     of 8 signals per launch (256 MiB, larger than L2).  The factor is the
     time against the 1-D transform of 2^22 points by this library
     (M = [[2^22]]), the comparison the table's factor column makes; the
-    library 1-D FFT of torch (cuFFT) is listed as context."""
+    library 1-D FFT of torch (cuFFT) is listed as context.  Each row is timed
+    with the direct route and with the route chosen at plan time
+    (PFFT_FLAG_AUTOTUNE: the forward transform of M may run as the adjoint
+    passes of M^T)."""
     w = SI.WORKLOADS["table1"]
     n, batch = w["n"], w["batch"]
     m = n * n
@@ -425,19 +428,23 @@ def bench_table1(pf, torch, peaks_hbm, steps=20, warmup=3):
     x = torch.randn(batch, m, dtype=torch.complex64, device="cuda", generator=gen) * math.sqrt(2.0)
     y = torch.empty_like(x)
 
-    def run(M):
-        plan = pf.PatternFFT(M, batch)
+    def run(M, route="direct"):
+        plan = pf.PatternFFT(M, batch, route=route)
         ms = _time_ms(torch, lambda: plan.forward(x, y), steps, warmup)
+        via = plan.route[0]
         plan.close()
-        return ms
+        return ms, via
 
-    ms_1d = run([[m]])
+    ms_1d, _ = run([[m]])
     ms_cufft = _time_ms(torch, lambda: torch.fft.fft(x, dim=1, norm="ortho"), steps, warmup)
     rows = []
     for i in TABLE1_I:
-        ms = run([[n, i], [0, n]])
+        ms, _ = run([[n, i], [0, n]])
+        ms_auto, via = run([[n, i], [0, n]], "auto")
         rows.append({"i": i, "ms_per_transform": ms / batch, "factor_vs_1d": ms / ms_1d,
                      "achieved_gbs_2pass": 2 * 16 * batch * m / (ms * 1e-3) / 1e9,
+                     "autotuned_ms_per_transform": ms_auto / batch, "autotuned_via_transpose": via,
+                     "autotuned_achieved_gbs_2pass": 2 * 16 * batch * m / (ms_auto * 1e-3) / 1e9,
                      "paper_serial_s": TABLE1_PAPER_SERIAL_S[i],
                      "paper_factor": TABLE1_PAPER_SERIAL_S[i] / TABLE1_PAPER_1D_S})
     return {"workload": "Table 1 family M = [[2048, i], [0, 2048]], 2^22 points, 8 signals per launch",

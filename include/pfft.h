@@ -101,7 +101,25 @@ enum {
    * d-dimensional DFT of sizes eps_1 .. eps_d (Theorem 1) without any
    * gather or scatter; the box extents reported by pfft_plan_info are the
    * eps_j.  Requires eps_d < 2^24. */
-  PFFT_FLAG_LAYOUT_SNF = 2u
+  PFFT_FLAG_LAYOUT_SNF = 2u,
+  /* Route each direction by measurement at plan time.  Read for M^T, eq.
+   * (Fouriermatrix) gives F(M^T) = F(M)^T with the two boxes exchanged, so
+   * the forward transform of M can run as the adjoint passes of M^T without
+   * their conjugations and the inverse of M as the forward passes of M^T
+   * with conjugated input and output; the passes of M^T walk other boxes and
+   * cycles and can be faster.  pfft_plan_create then also plans M^T, times
+   * each direction both ways (a few calls each, on two zeroed scratch
+   * buffers of |det M| * batch values allocated for the timing and freed
+   * after it, on a private stream) and keeps the plan of M^T, which shares
+   * this plan's workspace, only for a direction where it is at least 3%
+   * faster.  No effect with PFFT_FLAG_TC_SPLIT or PFFT_FLAG_LAYOUT_SNF, or
+   * when the transposed plan's row pass is the pipelined kernel (which runs
+   * only with the conjugations of its own directions). */
+  PFFT_FLAG_AUTOTUNE = 4u,
+  /* Run both directions through the plan of M^T (see PFFT_FLAG_AUTOTUNE)
+   * without timing.  PFFT_ERR_UNSUPPORTED in the cases where AUTOTUNE has
+   * no effect. */
+  PFFT_FLAG_TRANSPOSED = 8u
 };
 
 /* Which index map pfft_index_map returns. */
@@ -135,8 +153,8 @@ pfft_status pfft_smith_normal_form(int d, const int64_t* M, int64_t* Q, int64_t*
 
 /* Plan the transform on P(M) for `batch` signals of |det M| points each.
  * M: d*d row-major host array.  dtype: PFFT_C64 or PFFT_C128.  flags: any of
- * PFFT_FLAG_TC_SPLIT (PFFT_C64 only, else PFFT_ERR_UNSUPPORTED) and
- * PFFT_FLAG_LAYOUT_SNF.
+ * PFFT_FLAG_TC_SPLIT (PFFT_C64 only, else PFFT_ERR_UNSUPPORTED),
+ * PFFT_FLAG_LAYOUT_SNF, PFFT_FLAG_AUTOTUNE and PFFT_FLAG_TRANSPOSED.
  * Computes H(M), H(M^T), the Smith form and the basis of Theorem 1
  * (Section 3, eqs. (basisPM), (basisGM); Remark 2 allows any biorthogonal
  * pair, and the planner picks the one whose longest cycle runs along the
@@ -155,6 +173,11 @@ pfft_status pfft_plan_create(pfft_plan* out, int d, const int64_t* M, int64_t ba
  *   out_box : d extents of the output box (diagonal of H(M^T)) */
 pfft_status pfft_plan_info(pfft_plan p, int64_t* m, int* dM, int64_t* eps, int64_t* in_box,
                            int64_t* out_box);
+
+/* Route of each direction (PFFT_FLAG_AUTOTUNE / PFFT_FLAG_TRANSPOSED): *fwd,
+ * *inv = 1 when the forward / inverse transform runs through the plan of
+ * M^T, else 0.  Either pointer may be NULL.  Host only. */
+pfft_status pfft_plan_route(pfft_plan p, int* fwd, int* inv);
 
 /* Host copy of an index map (see PFFT_MAP_*).  coords: caller-owned host
  * array of m*d int64 (box maps) or m*dM int64 (Smith maps), slot-major. */

@@ -22,14 +22,14 @@ import torch
 from . import _capi
 from ._capi import (PFFT_BATCH_AUTOTUNE, PFFT_BATCH_NO_GRAPH, PFFT_BATCH_ONE_LAUNCH, PFFT_BATCH_RADIX8, PFFT_C64, PFFT_C128, PFFT_FLAG_LAYOUT_SNF,
                     pfft_batch_device_status, pfft_batch_set_wait_limit, pfft_batch_split_layout,
-                    PFFT_FLAG_TC_SPLIT,
+                    PFFT_FLAG_AUTOTUNE, PFFT_FLAG_TC_SPLIT, PFFT_FLAG_TRANSPOSED,
                     PFFT_MAP_INPUT_BOX,
                     PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_OUTPUT_SNF, PWT_DIRICHLET, PWT_DLVP,
                     PWT_FLAG_INPUT_SNF,
                     PfftError, pfft_batch_create, pfft_batch_destroy, pfft_batch_forward, pfft_batch_info,
                     pfft_batch_schedule, pfft_device_index_map, pwt_merge_general, pwt_split_general,
                     pfft_forward, pfft_hermite_normal_form, pfft_index_map, pfft_inverse, pfft_plan_create,
-                    pfft_last_device_status, pfft_plan_destroy, pfft_plan_info, pfft_profile_enable, pfft_profile_read,
+                    pfft_last_device_status, pfft_plan_destroy, pfft_plan_info, pfft_plan_route, pfft_profile_enable, pfft_profile_read,
                     pfft_set_wait_limit, pfft_smith_normal_form, pwt_adjoint, pwt_decompose, pwt_plan_create, pwt_plan_destroy,
                     pwt_plan_info, pwt_reconstruct)
 
@@ -41,6 +41,7 @@ __all__ = [
     "pwt_split_general", "pwt_merge_general",
     "PfftError", "PFFT_C64", "PFFT_C128", "PWT_DIRICHLET", "PWT_DLVP",
     "PFFT_MAP_INPUT_BOX", "PFFT_MAP_OUTPUT_BOX", "PFFT_MAP_INPUT_SNF", "PFFT_MAP_OUTPUT_SNF",
+    "PFFT_FLAG_AUTOTUNE", "PFFT_FLAG_TRANSPOSED", "pfft_plan_route",
     "pfft_plan_create", "pfft_plan_info", "pfft_index_map", "pfft_device_index_map", "pfft_forward",
     "pfft_inverse", "pfft_plan_destroy", "pfft_last_device_status", "pfft_set_wait_limit", "pfft_profile_enable", "pfft_profile_read",
     "pfft_hermite_normal_form", "pfft_smith_normal_form", "pwt_plan_create", "pwt_plan_info",
@@ -79,13 +80,19 @@ def _check_tensor(x: torch.Tensor, dtype, shape, name: str):
 class PatternFFT:
     """Plan of the transform on P(M) for ``batch`` signals (wraps pfft_plan)."""
 
-    def __init__(self, M, batch: int = 1, dtype=torch.complex64, tc_split: bool = False, layout: str = "box"):
+    def __init__(self, M, batch: int = 1, dtype=torch.complex64, tc_split: bool = False, layout: str = "box",
+                 route: str = "direct"):
         """``tc_split``: run the radix-16 / 32 stages on the tensor cores in
         split fp16 (PFFT_FLAG_TC_SPLIT; complex64 only).  ``layout``: "box"
         (Hermite boxes, the default) or "snf" (Smith coordinates,
-        PFFT_FLAG_LAYOUT_SNF)."""
+        PFFT_FLAG_LAYOUT_SNF).  ``route``: "direct" (the passes of M),
+        "auto" (each direction through the plan of M^T where that measures
+        faster, PFFT_FLAG_AUTOTUNE) or "transposed" (both directions through
+        it, PFFT_FLAG_TRANSPOSED)."""
         if layout not in ("box", "snf"):
             raise ValueError('layout must be "box" or "snf"')
+        if route not in ("direct", "auto", "transposed"):
+            raise ValueError('route must be "direct", "auto" or "transposed"')
         self.M = np.asarray(M, dtype=np.int64)
         self.d = int(self.M.shape[0])
         self.batch = int(batch)
@@ -93,12 +100,18 @@ class PatternFFT:
         self.tc_split = bool(tc_split)
         self.layout = layout
         flags = (PFFT_FLAG_TC_SPLIT if tc_split else 0) | (PFFT_FLAG_LAYOUT_SNF if layout == "snf" else 0)
+        flags |= {"direct": 0, "auto": PFFT_FLAG_AUTOTUNE, "transposed": PFFT_FLAG_TRANSPOSED}[route]
         self._h = pfft_plan_create(self.M, self.batch, _dtype_code(dtype), flags)
         self.m, self.dM, self.eps, self.in_box, self.out_box = pfft_plan_info(self._h, self.d)
 
     @property
     def shape(self):
         return (self.batch, self.m)
+
+    @property
+    def route(self):
+        """(forward, inverse): True where the direction runs through the plan of M^T."""
+        return pfft_plan_route(self._h)
 
     def forward(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """c_hat = F(M) c: x on the box of H(M), result on the box of H(M^T)."""

@@ -22,6 +22,8 @@ _lib = None
 PFFT_C64, PFFT_C128 = 0, 1
 PFFT_FLAG_TC_SPLIT = 1
 PFFT_FLAG_LAYOUT_SNF = 2
+PFFT_FLAG_AUTOTUNE = 4
+PFFT_FLAG_TRANSPOSED = 8
 PFFT_MAP_INPUT_BOX, PFFT_MAP_OUTPUT_BOX, PFFT_MAP_INPUT_SNF, PFFT_MAP_OUTPUT_SNF = 0, 1, 2, 3
 PWT_DIRICHLET, PWT_DLVP = 0, 1
 PWT_FLAG_INPUT_SNF = 1
@@ -53,6 +55,7 @@ _SIGS = {
     "pfft_plan_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64p, ctypes.c_int64,
                                         ctypes.c_int, ctypes.c_uint]),
     "pfft_plan_info": (ctypes.c_int, [_vp, _i64p, ctypes.POINTER(ctypes.c_int), _i64p, _i64p, _i64p]),
+    "pfft_plan_route": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "pfft_index_map": (ctypes.c_int, [_vp, ctypes.c_int, _i64p]),
     "pfft_device_index_map": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "pfft_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -165,6 +168,12 @@ def pfft_plan_info(plan, d: int):
     ob, op = _i64(np.zeros(d))
     _check(lib().pfft_plan_info(plan, ctypes.byref(m), ctypes.byref(dM), ep, ip, op), "pfft_plan_info")
     return m.value, dM.value, eps, ib, ob
+
+
+def pfft_plan_route(plan):
+    fwd, inv = ctypes.c_int(), ctypes.c_int()
+    _check(lib().pfft_plan_route(plan, ctypes.byref(fwd), ctypes.byref(inv)), "pfft_plan_route")
+    return bool(fwd.value), bool(inv.value)
 
 
 def pfft_index_map(plan, which: int, m: int, width: int):

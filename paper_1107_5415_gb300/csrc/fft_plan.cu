@@ -845,6 +845,10 @@ pfft_status pfft::plan_retile(pfft_plan_s& P, int row_budget, int col_budget, in
 
 void pfft::plan_release(pfft_plan_s* P) {
   if (!P) return;
+  if (P->tr) {
+    P->tr->ws = nullptr;  // this plan's workspace
+    plan_release(P->tr);
+  }
   if (!P->arena) {
     for (void* p : {(void*)P->dtab, P->tw, P->tw_col, P->ws, P->stw, P->fs_tab, (void*)P->runs, (void*)P->status})
       if (p) cudaFree(p);
@@ -852,11 +856,13 @@ void pfft::plan_release(pfft_plan_s* P) {
   delete P;
 }
 static void release(pfft_plan_s* P) { plan_release(P); }
+static pfft_status plan_route(pfft_plan_s& P, int d, const int64_t* M, unsigned flags);
 
 extern "C" pfft_status pfft_plan_create(pfft_plan* out, int d, const int64_t* M, int64_t batch,
                                         int dtype, unsigned flags) {
   if (!out || !M || batch < 1 || batch > 65535 || (dtype != PFFT_C64 && dtype != PFFT_C128) ||
-      (flags & ~unsigned(PFFT_FLAG_TC_SPLIT | PFFT_FLAG_LAYOUT_SNF)) || d < 1 || d > 4)
+      (flags & ~unsigned(PFFT_FLAG_TC_SPLIT | PFFT_FLAG_LAYOUT_SNF | PFFT_FLAG_AUTOTUNE | PFFT_FLAG_TRANSPOSED)) ||
+      d < 1 || d > 4)
     return PFFT_ERR_ARG;
   if ((flags & PFFT_FLAG_TC_SPLIT) && dtype != PFFT_C64) return PFFT_ERR_UNSUPPORTED;
   *out = nullptr;
@@ -894,6 +900,7 @@ extern "C" pfft_status pfft_plan_create(pfft_plan* out, int d, const int64_t* M,
   } catch (const LatticeError& e) {
     st = pfft_status(e.code);
   }
+  if (st == PFFT_OK && (flags & (PFFT_FLAG_AUTOTUNE | PFFT_FLAG_TRANSPOSED))) st = plan_route(*P, d, M, flags);
   if (st != PFFT_OK) {
     release(P);
     return st;
@@ -905,6 +912,13 @@ extern "C" pfft_status pfft_plan_create(pfft_plan* out, int d, const int64_t* M,
 extern "C" pfft_status pfft_plan_destroy(pfft_plan p) {
   if (!p) return PFFT_ERR_ARG;
   release(p);
+  return PFFT_OK;
+}
+
+extern "C" pfft_status pfft_plan_route(pfft_plan p, int* fwd, int* inv) {
+  if (!p) return PFFT_ERR_ARG;
+  if (fwd) *fwd = p->tr && p->tr_fwd ? 1 : 0;
+  if (inv) *inv = p->tr && p->tr_inv ? 1 : 0;
   return PFFT_OK;
 }
 
@@ -981,15 +995,36 @@ static pfft_status run_pass(pfft_plan_s* P, PassArgs a, int load, int store, int
   return PFFT_OK;
 }
 
-static pfft_status transform(pfft_plan p, const void* in, void* out, void* stream, bool inverse) {
-  if (!p || !in || !out || in == out) return PFFT_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
+// The transform of p through the plan t = p->tr of M^T (see pfft_plan_s::tr):
+// forward = t's adjoint passes without conjugations, inverse = t's forward
+// passes with conjugated input and output.  Kernel time is recorded under p.
+static pfft_status transform_transposed(pfft_plan p, const void* in, void* out, cudaStream_t s, bool inverse) {
+  pfft_plan_s* t = p->tr;
+  const double scale = 1.0 / std::sqrt(double(p->m));
+  const int c = inverse ? 1 : 0;
+  if (t->pen.empty()) {
+    return run_pass(p, t->rowp, inverse ? MAP_BOX_H : MAP_BOX_G, inverse ? MAP_BOX_G : MAP_BOX_H, c, c, scale, in,
+                    out, s, 0);
+  }
+  if (inverse) {
+    pfft_status st = run_pass(p, t->rowp, MAP_BOX_H, MAP_WS, 1, 0, 1.0, in, t->ws, s, 0);
+    if (st != PFFT_OK) return st;
+    return run_pass(p, t->colp, MAP_WS, MAP_BOX_G, 0, 1, scale, t->ws, out, s, 1);
+  }
+  pfft_status st = run_pass(p, t->colp, MAP_BOX_G, MAP_WS, 0, 0, 1.0, in, t->ws, s, 1);
+  if (st != PFFT_OK) return st;
+  return run_pass(p, t->rowp, MAP_WS, MAP_BOX_H, 0, 0, scale, t->ws, out, s, 0);
+}
+
+static pfft_status transform_route(pfft_plan p, const void* in, void* out, cudaStream_t s, bool inverse,
+                                   bool via_tr) {
   const double scale = 1.0 / std::sqrt(double(p->m));
   if (p->D == 0) {
     const size_t bytes = size_t(p->batch) * elem_bytes(p->dtype);
     return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? PFFT_OK
                                                                                        : PFFT_ERR_CUDA;
   }
+  if (via_tr) return transform_transposed(p, in, out, s, inverse);
   const int ci = inverse ? 1 : 0;
   if (p->pen.empty()) {
     return run_pass(p, p->rowp, inverse ? MAP_BOX_G : MAP_BOX_H, inverse ? MAP_BOX_H : MAP_BOX_G, ci, ci,
@@ -1003,6 +1038,106 @@ static pfft_status transform(pfft_plan p, const void* in, void* out, void* strea
   pfft_status st = run_pass(p, p->colp, MAP_BOX_G, MAP_WS, 1, 0, 1.0, in, p->ws, s, 1);
   if (st != PFFT_OK) return st;
   return run_pass(p, p->rowp, MAP_WS, MAP_BOX_H, 0, 1, scale, p->ws, out, s, 0);
+}
+
+static pfft_status transform(pfft_plan p, const void* in, void* out, void* stream, bool inverse) {
+  if (!p || !in || !out || in == out) return PFFT_ERR_ARG;
+  const bool via_tr = p->tr && (inverse ? p->tr_inv : p->tr_fwd);
+  return transform_route(p, in, out, (cudaStream_t)stream, inverse, via_tr);
+}
+
+// Mean time (ms) of one direction by one route over `reps` calls on stream s;
+// negative when a call fails.
+static float time_route(pfft_plan_s* p, bool inverse, bool via_tr, const void* in, void* out, cudaStream_t s,
+                        int reps) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return -1.0f;
+  }
+  float ms = -1.0f;
+  bool ok = transform_route(p, in, out, s, inverse, via_tr) == PFFT_OK;  // warm-up
+  ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+  for (int r = 0; ok && r < reps; ++r) ok = transform_route(p, in, out, s, inverse, via_tr) == PFFT_OK;
+  ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+       cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    return -1.0f;
+  }
+  return ms / float(reps);
+}
+
+// PFFT_FLAG_TRANSPOSED / PFFT_FLAG_AUTOTUNE: plan M^T beside M (same batch and
+// precision, this plan's workspace and status word) and route the directions
+// through it, always (TRANSPOSED) or where it measures faster (AUTOTUNE: each
+// direction timed both ways on zeroed scratch buffers; the transposed route
+// must win by 3%).  Plans of the Smith layout or the split-precision form,
+// and transposed plans whose row pass is the pipelined kernel (which runs
+// only with the conjugations of its own directions), keep the direct route:
+// PFFT_ERR_UNSUPPORTED under TRANSPOSED, silently under AUTOTUNE.
+static pfft_status plan_route(pfft_plan_s& P, int d, const int64_t* M, unsigned flags) {
+  const bool force = (flags & PFFT_FLAG_TRANSPOSED) != 0;
+  const pfft_status no = force ? PFFT_ERR_UNSUPPORTED : PFFT_OK;
+  if (P.tc || (flags & PFFT_FLAG_LAYOUT_SNF) || P.D == 0) return no;
+  std::vector<int64_t> Mt(size_t(d) * d);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) Mt[size_t(i) * d + j] = M[size_t(j) * d + i];
+  pfft_plan_s* T = new (std::nothrow) pfft_plan_s;
+  if (!T) return PFFT_ERR_OOM;
+  T->batch = P.batch;
+  T->dtype = P.dtype;
+  T->own_workspace = false;
+  pfft_status st;
+  try {
+    st = plan_host(*T, d, Mt.data());
+    if (st == PFFT_OK) st = plan_device(*T);
+  } catch (const LatticeError& e) {
+    st = pfft_status(e.code);
+  }
+  if (st == PFFT_OK && (T->rowp.pipe || T->pen.size() != P.pen.size())) st = PFFT_ERR_UNSUPPORTED;
+  if (st != PFFT_OK) {
+    plan_release(T);
+    return force ? st : PFFT_OK;
+  }
+  T->ws = P.ws;
+  T->rowp.status = T->colp.status = P.status;
+  P.tr = T;
+  if (force) {
+    P.tr_fwd = P.tr_inv = true;
+    return PFFT_OK;
+  }
+  // AUTOTUNE: time both routes of each direction
+  const size_t bytes = size_t(P.m) * size_t(P.batch) * elem_bytes(P.dtype);
+  void *a = nullptr, *b = nullptr;
+  cudaStream_t s = nullptr;
+  bool ok = cudaMalloc(&a, bytes) == cudaSuccess && cudaMalloc(&b, bytes) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaMemsetAsync(a, 0, bytes, s) == cudaSuccess;
+  if (ok) {
+    const int reps = 3;
+    for (int inv = 0; inv < 2; ++inv) {
+      const float direct = time_route(&P, inv != 0, false, a, b, s, reps);
+      const float via = time_route(&P, inv != 0, true, a, b, s, reps);
+      const bool use = direct > 0.0f && via > 0.0f && via < 0.97f * direct;
+      (inv ? P.tr_inv : P.tr_fwd) = use;
+    }
+    cudaStreamSynchronize(s);
+  }
+  cudaGetLastError();
+  if (s) cudaStreamDestroy(s);
+  if (a) cudaFree(a);
+  if (b) cudaFree(b);
+  if (!P.tr_fwd && !P.tr_inv) {
+    T->ws = nullptr;
+    plan_release(T);
+    P.tr = nullptr;
+  }
+  return PFFT_OK;
 }
 
 extern "C" pfft_status pfft_forward(pfft_plan p, const void* in, void* out, void* stream) {
@@ -1029,7 +1164,9 @@ extern "C" pfft_status pfft_profile_read(pfft_plan p, const char** names, int64_
 extern "C" pfft_status pfft_set_wait_limit(pfft_plan p, int64_t spins) {
   if (!p) return PFFT_ERR_ARG;
   if (!p->rowp.tma) return PFFT_ERR_UNSUPPORTED;
-  p->rowp.spin_limit = spins < 0 ? kSpinLimit : uint32_t(std::min<int64_t>(spins, int64_t(UINT32_MAX)));
+  const uint32_t lim = spins < 0 ? kSpinLimit : uint32_t(std::min<int64_t>(spins, int64_t(UINT32_MAX)));
+  p->rowp.spin_limit = lim;
+  if (p->tr) p->tr->rowp.spin_limit = lim;
   return PFFT_OK;
 }
 

@@ -45,6 +45,14 @@ struct pfft_plan_s {
   int* status = nullptr;  // device status word
   pfft::PassArgs rowp{}, colp{};
   pfft::Profiler prof;
+  // Transposed route.  Entry (k, y) of F(M) is entry (y, k) of F(M^T) in box
+  // order (eq. (Fouriermatrix) read for M^T), so the forward transform of M
+  // is the adjoint passes of M^T without their conjugations and the inverse
+  // of M is the forward passes of M^T with conjugated input and output.  tr
+  // is the plan of M^T (sharing this plan's workspace and status word);
+  // tr_fwd / tr_inv: the direction runs through it.
+  pfft_plan_s* tr = nullptr;
+  bool tr_fwd = false, tr_inv = false;
 
   int alloc(void** p, size_t bytes) { return arena ? arena->alloc(p, bytes) : pfft::device_alloc(p, bytes); }
 };

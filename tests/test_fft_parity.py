@@ -153,6 +153,23 @@ def test_batched_2d_sampled_frequencies():
     assert rel_l2(back.cpu().numpy(), c) <= 1e-5
 
 
+@pytest.mark.parametrize("M,batch", [(SI.M_BATCHED_2D, 2), ([[64, 16], [-16, 64]], 4), ([[5, -2], [3, 7]], 3),
+                                     ([[32, 5, 7], [0, 64, 9], [0, 0, 8192]], 1), (SI.M_AUTOGRAD_3D, 1)])
+def test_inverse_equals_conjugated_forward_of_the_transpose(M, batch):
+    """F(M^T) = F(M)^T in box order (eq. (Fouriermatrix) read for M^T), so the
+    inverse of M equals the conjugated forward transform of M^T: two plans whose
+    passes walk different boxes and cycles must agree to rounding."""
+    A = pf.PatternFFT(M, batch)
+    B = pf.PatternFFT(L.transpose(M), batch)
+    assert A.m == B.m
+    y = _gpu(SI.complex_normal(batch, A.m, 21))
+    back = A.inverse(y)
+    alt = torch.conj(B.forward(torch.conj(y).resolve_conj())).resolve_conj()
+    A.check_device_status()
+    B.check_device_status()
+    assert (torch.linalg.vector_norm(back - alt) / torch.linalg.vector_norm(back)).item() <= 1e-5
+
+
 def test_autograd_3d_sampled_frequencies():
     w = SI.WORKLOADS["autograd_3d"]
     M, batch = w["M"], w["batch"]
@@ -204,6 +221,49 @@ def test_table1_shapes_sampled(i):
     back = plan.inverse(_gpu(y)).cpu().numpy()
     assert rel_l2(back, c) <= 1e-5
     assert np.allclose(np.linalg.norm(y, axis=1), np.linalg.norm(c, axis=1), rtol=1e-5)
+
+
+@pytest.mark.parametrize("M", SMALL, ids=[str(i) for i in range(len(SMALL))])
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_transposed_route_full(M, dtype):
+    """PFFT_FLAG_TRANSPOSED: both directions through the plan of M^T (its
+    adjoint passes without conjugations, its forward passes with conjugated
+    input and output), compared with the oracle on every output."""
+    m = abs(L.det(M))
+    batch = 3
+    try:
+        plan = pf.PatternFFT(M, batch, dtype, route="transposed")
+    except pf.PfftError as e:
+        if e.status == 5:
+            pytest.skip(f"no transposed route: {e}")
+        raise
+    assert plan.route == (True, True)
+    npdt = np.complex64 if dtype == torch.complex64 else np.complex128
+    c = SI.complex_normal(batch, m, seed=m % 89, dtype=npdt)
+    ref = oracle.pattern_fft(M, c)
+    tol = TOL["c64" if dtype == torch.complex64 else "c128"]
+    assert rel_l2(plan.forward(_gpu(c)).cpu().numpy(), ref) <= tol
+    back = plan.inverse(_gpu(ref.astype(npdt))).cpu().numpy()
+    assert rel_l2(back, oracle.pattern_fft(M, ref, inverse=True)) <= tol
+    plan.check_device_status()
+
+
+@pytest.mark.parametrize("M,batch", [([[2048, 2], [0, 2048]], 2), ([[2048, 16], [0, 2048]], 2),
+                                     ([[2048, 1], [0, 2048]], 2), (SI.M_BATCHED_2D, 2),
+                                     ([[32, 5, 7], [0, 64, 9], [0, 0, 8192]], 1)])
+def test_autotuned_route_sampled(M, batch):
+    """PFFT_FLAG_AUTOTUNE at full size: whichever route each direction took,
+    sampled frequencies against the oracle's direct sum and the round trip."""
+    plan = pf.PatternFFT(M, batch, route="auto")
+    m = plan.m
+    c = SI.complex_normal(batch, m, 31)
+    y = plan.forward(_gpu(c)).cpu().numpy()
+    slots = SI.sample_slots(m, 512, seed=3)
+    assert rel_l2(y[batch - 1:batch, slots], oracle.pattern_fft(M, c[batch - 1:batch], out_slots=slots)) <= 1e-5
+    back = plan.inverse(_gpu(y)).cpu().numpy()
+    assert rel_l2(back, c) <= 1e-5
+    plan.check_device_status()
+    assert all(isinstance(r, bool) for r in plan.route)
 
 
 def test_long_cycle_fp64_full():

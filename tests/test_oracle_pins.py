@@ -102,6 +102,23 @@ def test_parseval_and_inverse_identity(seed):
     assert np.allclose(oracle.pattern_fft(M, ch, inverse=True), c, atol=1e-12)
 
 
+@pytest.mark.parametrize("M", [[[5, -2], [3, 7]], [[6, 2], [0, 9]], [[4, 1], [0, 4]],
+                               [[3, 1, 2], [0, 4, 1], [0, 0, 2]], [[2, 1, 0], [1, 3, 1], [0, 1, 4]]])
+def test_transposed_pattern_gives_the_transposed_matrix(M):
+    """Eq. (Fouriermatrix): entry (k, y) of F(M) is m^{-1/2} exp(-2 pi i k^T M^{-1} y),
+    k in G(M^T), y indexing P(M); the same expression read for M^T is entry (y, k) of
+    F(M^T) with the roles of the two boxes exchanged.  So F(M^T) = F(M)^T in box
+    order, and the inverse of M is the conjugated forward transform of M^T."""
+    Mt = L.transpose(M)
+    m = abs(L.det(M))
+    F = oracle.pattern_fft(M, np.eye(m, dtype=complex)).T    # column j = F(M) e_j
+    Ft = oracle.pattern_fft(Mt, np.eye(m, dtype=complex)).T
+    assert np.allclose(Ft, F.T, atol=1e-12)
+    c = _rand_c(m, 2, 7)
+    assert np.allclose(np.conj(oracle.pattern_fft(Mt, np.conj(c))), oracle.pattern_fft(M, c, inverse=True),
+                       atol=1e-12)
+
+
 @pytest.mark.parametrize("M", [SI.M_SMALL_2D, [[6, 2], [-2, 6]], [[4, 0], [0, 2]],
                                SI.M_AUTOGRAD_TINY, [[3, 1, 2], [0, 2, 1], [1, 0, 4]],
                                [[8, 2], [2, -4]], [[8, 8], [-8, 8]]])
