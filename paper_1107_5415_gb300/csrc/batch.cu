@@ -191,6 +191,18 @@ pfft_status build_schedule(pfft_batch_s& B) {
     std::memcpy(host.data() + o, p, bytes);
     return o;
   };
+  // prefix table of first CTAs (n + 1 ints, padded to an even count), then
+  // the (item, tile) pair of every CTA (cta_item in batch_kernels.cu)
+  auto with_map = [](std::vector<int> c0) {
+    const int n = int(c0.size()) - 1;
+    if (c0.size() & 1) c0.push_back(0);
+    for (int k = 0; k < n; ++k)
+      for (int t = 0; t < c0[k + 1] - c0[k]; ++t) {
+        c0.push_back(k);
+        c0.push_back(t);
+      }
+    return c0;
+  };
   auto put_group = [&](Bucket& b, const std::vector<Item>& v) {
     std::vector<PassArgs> a(v.size());
     std::vector<int> c0(v.size() + 1, 0);
@@ -199,7 +211,8 @@ pfft_status build_schedule(pfft_batch_s& B) {
       c0[k + 1] = c0[k] + v[k].a.groups;
     }
     b.items_off = put(a.data(), a.size() * sizeof(PassArgs));
-    b.cta0_off = put(c0.data(), c0.size() * sizeof(int));
+    const std::vector<int> t = with_map(c0);
+    b.cta0_off = put(t.data(), t.size() * sizeof(int));
   };
   for (size_t k = 0; k < rb.size(); ++k) put_group(rb[k], rg[k]);
   for (size_t k = 0; k < cb.size(); ++k) put_group(cb[k], cg[k]);
@@ -216,7 +229,8 @@ pfft_status build_schedule(pfft_batch_s& B) {
     b.nctas = c0.back();
     b.threads = kSplitThreads;
     b.items_off = put(si.data(), si.size() * sizeof(SplitItem));
-    b.cta0_off = put(c0.data(), c0.size() * sizeof(int));
+    const std::vector<int> t = with_map(c0);
+    b.cta0_off = put(t.data(), t.size() * sizeof(int));
     sb.push_back(b);
   }
   // prime split launch: one item per pattern with |det J| > 2, costliest first
@@ -237,7 +251,8 @@ pfft_status build_schedule(pfft_batch_s& B) {
     b.nctas = c0.back();
     b.threads = kSplitThreads;
     b.items_off = put(pi.data(), pi.size() * sizeof(PrimeItem));
-    b.cta0_off = put(c0.data(), c0.size() * sizeof(int));
+    const std::vector<int> t = with_map(c0);
+    b.cta0_off = put(t.data(), t.size() * sizeof(int));
     pb.push_back(b);
   }
   // the single-launch queue: rows, columns, p = 2 splits, prime splits, each

@@ -17,8 +17,10 @@ constexpr int kSplitPerThread = 4;  // fibres per thread of a grouped split CTA
 constexpr int kGroupedMaxDynSmem = 227 * 1024 - 4096;
 
 // One grouped pass launch: items[k] is the descriptor of the k-th pattern of
-// the launch, whose tiles are CTAs cta0[k] .. cta0[k+1]-1.  The in / out
-// fields of an item hold byte offsets into base[in_sel] / base[out_sel].
+// the launch, whose tiles are CTAs cta0[k] .. cta0[k+1]-1; after the n + 1
+// entries of cta0 (padded to an even count) the (item, tile) pair of every
+// CTA.  The in / out fields of an item hold byte offsets into base[in_sel] /
+// base[out_sel].
 struct GroupArgs {
   const PassArgs* items;
   const int* cta0;
@@ -91,11 +93,13 @@ int launch_batch_queue(const QueueArgs& g, int dtype, int nunits, int smem, cuda
 int prepare_grouped(int dtype);
 int launch_grouped_pass(const GroupArgs& g, int cols, int dtype, int nctas, int threads, int smem,
                         cudaStream_t s);
+// The split levels of the patterns with |det J| = 2 (cta0 and the CTA map as
+// in GroupArgs).
 int launch_grouped_split(const SplitItem* items, const int* cta0, int n, int nctas, const void* chat, void* sc,
                          void* wv, int dtype, cudaStream_t s);
 // The split levels of the patterns with |det J| > 2: items[k]'s work items
 // (fibre, chunk of kPrimeChunk bands) start at CTA cta0[k], kSplitThreads
-// items per CTA.
+// items per CTA (cta0 and the CTA map as in GroupArgs).
 int launch_grouped_prime_split(const PrimeItem* items, const int* cta0, int n, int nctas, const void* chat,
                                void* sc, void* wv, int dtype, cudaStream_t s);
 

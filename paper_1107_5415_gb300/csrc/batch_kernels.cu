@@ -24,6 +24,13 @@ __device__ __forceinline__ int find_item(const int* __restrict__ cta0, int n, in
   return lo;
 }
 
+// Item k and tile t of CTA b (CTAs cta0[k] .. cta0[k+1]-1 run item k): the
+// pair stored for b after the prefix table (n + 1 ints, padded to an even
+// count), one load instead of a search.
+__device__ __forceinline__ int2 cta_item(const int* __restrict__ cta0, int n, int b) {
+  return __ldg(reinterpret_cast<const int2*>(cta0 + ((n + 2) & ~1)) + b);
+}
+
 template <typename T>
 __device__ __forceinline__ void copy_to_smem(T* dst, const T* src) {
   static_assert(sizeof(T) % 16 == 0, "descriptor size must be a multiple of 16 bytes");
@@ -36,15 +43,15 @@ template <typename C, int EPT, bool COLS, int MINB>
 __global__ void __launch_bounds__(kMaxThreads, MINB) grouped_pass_kernel(GroupArgs g) {
   __shared__ PassArgs a;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int it = find_item(g.cta0, g.n, blockIdx.x);
-  copy_to_smem(&a, g.items + it);
+  const int2 kt = cta_item(g.cta0, g.n, blockIdx.x);
+  copy_to_smem(&a, g.items + kt.x);
   __syncthreads();
   if (threadIdx.x == 0) {
     a.in = static_cast<const char*>(g.base[a.in_sel]) + reinterpret_cast<uintptr_t>(a.in);
     a.out = static_cast<char*>(const_cast<void*>(g.base[a.out_sel])) + reinterpret_cast<uintptr_t>(a.out);
   }
   __syncthreads();
-  const int tile = blockIdx.x - __ldg(g.cta0 + it);
+  const int tile = kt.y;
   C* sm = reinterpret_cast<C*>(smem_raw);
   if constexpr (COLS) {
     if (a.pad)
@@ -65,10 +72,10 @@ __global__ void __launch_bounds__(kSplitThreads) grouped_split_kernel(const Spli
                                                                       const C* __restrict__ chat,
                                                                       C* __restrict__ sc, C* __restrict__ wv) {
   __shared__ SplitItem it;
-  const int k = find_item(cta0, n, blockIdx.x);
-  copy_to_smem(&it, items + k);
+  const int2 kt = cta_item(cta0, n, blockIdx.x);
+  copy_to_smem(&it, items + kt.x);
   __syncthreads();
-  const int g0 = (blockIdx.x - __ldg(cta0 + k)) * (kSplitThreads * kSplitPerThread) + threadIdx.x;
+  const int g0 = kt.y * (kSplitThreads * kSplitPerThread) + threadIdx.x;
   const C* cin = chat + it.in_off;
   C* d1 = sc + it.sc_off;
   C* d2 = wv + it.wv_off;
@@ -89,10 +96,10 @@ __global__ void __launch_bounds__(kSplitThreads) grouped_prime_kernel(const Prim
                                                                       const C* __restrict__ chat,
                                                                       C* __restrict__ sc, C* __restrict__ wv) {
   __shared__ PrimeItem it;
-  const int k = find_item(cta0, n, blockIdx.x);
-  copy_to_smem(&it, items + k);
+  const int2 kt = cta_item(cta0, n, blockIdx.x);
+  copy_to_smem(&it, items + kt.x);
   __syncthreads();
-  const long long w = (long long)(blockIdx.x - __ldg(cta0 + k)) * kSplitThreads + threadIdx.x;
+  const long long w = (long long)kt.y * kSplitThreads + threadIdx.x;
   const long long mN = it.P.mN;
   if (w >= mN * it.P.nch) return;
   const int ch = int(w / mN), gs = int(w - ch * mN);
