@@ -1,8 +1,10 @@
 // Grouped launches of a pattern batch: one launch runs the same pass for many
-// patterns of different size.  Each CTA finds its pattern in a prefix table of
-// first-CTA indices, copies that pattern's pass descriptor into shared memory
-// and runs the generic (shared-memory Stockham) pass body of fft_kernels.cuh
-// or the split butterfly of wavelet_kernels.cuh on its tile.
+// patterns of different size.  Each CTA reads its pattern and tile from a
+// per-CTA map stored after the launch's prefix table of first-CTA indices,
+// copies that pattern's pass descriptor into shared memory and runs the
+// generic (shared-memory Stockham) pass body of fft_kernels.cuh or the split
+// butterfly of wavelet_kernels.cuh on its tile.  The single-launch queue
+// kernel finds the pattern of a work unit by a search of its prefix table.
 #include <cuda_runtime.h>
 
 #include "batch.hpp"
