@@ -454,6 +454,44 @@ def bench_table1(pf, torch, peaks_hbm, steps=20, warmup=3):
             "rows": rows}
 
 
+def bench_autograd3d(pf, torch, peaks_hbm, steps=20, warmup=3):
+    """The 3-D workload with autograd: M = [[256,64,0],[0,256,32],[0,0,256]]
+    (cycles 32, 64, 8192), batch 4, complex64.  Times the forward and the
+    inverse transform (two passes each, 16 B per point and pass compulsory)
+    and one gradient step of loss = sum |w * F c|^2 with real weights w (the
+    forward transform, the loss, and the backward pass through the inverse
+    kernels)."""
+    w = SI.WORKLOADS["autograd_3d"]
+    M, batch = w["M"], w["batch"]
+    plan = pf.PatternFFT(M, batch)
+    m = plan.m
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w["seed"])
+    x = torch.randn(batch, m, dtype=torch.complex64, device="cuda", generator=gen)
+    wt = torch.rand(batch, m, device="cuda", generator=gen)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    fwd = _time_ms(torch, lambda: plan.forward(x, y), steps, warmup)
+    inv = _time_ms(torch, lambda: plan.inverse(y, z), steps, warmup)
+    xg = x.clone().requires_grad_(True)
+
+    def grad_step():
+        xg.grad = None
+        loss = (wt * pf.pattern_fft(xg, plan).abs() ** 2).sum()
+        loss.backward()
+
+    step = _time_ms(torch, grad_step, steps, warmup)
+    pts = batch * m
+    comp = lambda ms: 2 * 16 * pts / (ms * 1e-3) / 1e9
+    out = {"workload": "3-D pattern FFT, M = [[256,64,0],[0,256,32],[0,0,256]], batch 4, complex64",
+           "forward_ms": fwd, "inverse_ms": inv, "grad_step_ms": step,
+           "forward_points_per_s": pts / (fwd * 1e-3),
+           "forward_compulsory_gbs": comp(fwd), "forward_compulsory_frac": comp(fwd) / peaks_hbm,
+           "inverse_compulsory_frac": comp(inv) / peaks_hbm}
+    plan.close()
+    return out
+
+
 def bench_directional(pf, torch, peaks_hbm, steps=20, warmup=3):
     """One split level of M = 512 I by each dilation of Section 6.2's set
     {J_x, J_y, J_d} (Dirichlet symbol), 16 signals of anisotropic synthetic
@@ -643,6 +681,7 @@ def run_native(args):
     wavelet = None if args.no_wavelet else bench_wavelet(pf, torch, peaks_hbm=peaks_hbm)
     mix = None if args.no_mix else bench_mix(pf, torch, peaks_hbm=peaks_hbm, n_patterns=args.mix_patterns)
     table1 = None if args.no_table1 else bench_table1(pf, torch, peaks_hbm)
+    autograd3d = None if args.no_table1 else bench_autograd3d(pf, torch, peaks_hbm)
     directional = None if args.no_directional else bench_directional(pf, torch, peaks_hbm)
     if args.no_e2e:
         e2e_value, e2e_ms = None, None
@@ -651,7 +690,7 @@ def run_native(args):
             print(json.dumps({"metric": METRIC, "value": value, "unit": "points/s", "ms_per_step": ms_max,
                               "kernels": prof, "tc_split": tc, "snf_layout": snf_layout, "wavelet": wavelet,
                               "uneven_mix": mix,
-                              "table1": table1, "directional": directional,
+                              "table1": table1, "autograd_3d": autograd3d, "directional": directional,
                               "note": "profiling run (no e2e)"}), flush=True)
         return 0
     # end to end through the public API with host buffers (pinned), per step:
@@ -753,6 +792,7 @@ def run_native(args):
             "wavelet": wavelet,
             "uneven_mix": mix,
             "table1": table1,
+            "autograd_3d": autograd3d,
             "directional": directional,
             "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": int(x.numel() * 8),
                     "d2h_bytes_per_step": int(z.numel() * 8),
@@ -783,7 +823,8 @@ def main(argv=None):
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core form measurement")
     ap.add_argument("--mix-patterns", type=int, default=0,
                     help="first N patterns of the uneven mix only (profiling runs; default all 4096)")
-    ap.add_argument("--no-table1", action="store_true", help="skip the Table 1 pattern sweep")
+    ap.add_argument("--no-table1", action="store_true",
+                    help="skip the Table 1 pattern sweep and the 3-D autograd workload")
     ap.add_argument("--no-directional", action="store_true", help="skip the directional dilation comparison")
     ap.add_argument("--batch", type=int, default=0, help="override the workload batch (profiling runs)")
     args = ap.parse_args(argv)

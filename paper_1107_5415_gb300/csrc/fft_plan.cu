@@ -213,6 +213,27 @@ bool tile_fits(int L, int row_max, int ept) {
   return threads_for(p, ept) <= kMaxThreads;
 }
 
+// Register-resident column pass over two pencil axes (fft_fast2.cuh): the
+// 2-D DFT of sizes top x low (top the slower axis of the row index) is the
+// 1-D Stockham DFT of length L = top low without the twiddles that couple the
+// axes, provided the first stages' radices multiply to top -- a radix-32
+// complex64 pass of L = t 32^s (tail t first) has those products t 32^j,
+// j < s.  Box layout, complex64, no split-precision stages, no four-step
+// split, both axes powers of two.
+bool fast2_axes(const pfft_plan_s& P, int top, int low) {
+  if (P.dtype != PFFT_C64 || P.tc || P.generic_only || P.fs_na != 1 || P.pen.size() != 2) return false;
+  if (top < 2 || low < 2 || (top & (top - 1)) || (low & (low - 1))) return false;
+  const int L = top * low;
+  if (L < 64 || L > 16384) return false;
+  int lg = 0;
+  while ((1 << lg) < L) ++lg;
+  const int nmain = lg / 5;
+  int b = 1 << (lg - 5 * nmain);
+  for (int j = 0; j < nmain; ++j, b *= 32)
+    if (b == top) return true;
+  return false;
+}
+
 pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) {
   const int ept = P.dtype == PFFT_C64 ? P.ept_c64 : 16;
   p.cols = cols;
@@ -249,7 +270,7 @@ pfft_status configure_pass(PassArgs& p, const pfft_plan_s& P, bool cols, int T) 
     // split-precision plans use them too, their radix-32 main stages on the tensor cores
     const bool tc_fast = P.tc && P.dtype == PFFT_C64 && p.tw_n % 32 == 0;
     // (a column tile of the register-resident pass holds T whole columns: T divides nD)
-    p.fast = ((!P.generic_only || tc_fast) && p.tw_n == P.nD && p.pow2 && pow2L && P.d <= 3 && (!cols || P.pen.size() == 1) && (!cols || P.nD % T == 0) && T * L <= (P.dtype == PFFT_C64 ? 16384 : 8192)) ? 1 : 0;
+    p.fast = ((!P.generic_only || tc_fast) && p.tw_n == P.nD && p.pow2 && pow2L && P.d <= 3 && (!cols || P.pen.size() == 1 || fast2_axes(P, P.pen[0], P.pen[1])) && (!cols || P.nD % T == 0) && T * L <= (P.dtype == PFFT_C64 ? 16384 : 8192)) ? 1 : 0;
     if (p.fast) {
       int lg = 0, lr = 0;
       while ((1 << lg) < L) ++lg;
@@ -488,12 +509,21 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
   const int nD = P.nD, LB = P.LB;
   const int na = P.fs_na;
   const int npen = int(P.pen.size());
+  // two pencil axes of which only the faster one starts a register-resident
+  // column pass (fast2_axes): make it the slower axis of the row index (the
+  // rows then run over (lambda_2, lambda_1); the tables below follow)
+  const bool swap2 = npen == 2 && na == 1 && !fast2_axes(P, P.pen[0], P.pen[1]) && fast2_axes(P, P.pen[1], P.pen[0]);
+  if (swap2) std::swap(P.pen[0], P.pen[1]);
   // Row (A, B) and column (C, E) generator lists of the logical LB x nD array:
   //   row index  = flatten(lambda_1..lambda_{D-1}[, lambda_a]),  element = lambda_b
   //   col index  = flatten(mu_1..mu_{D-1}[, mu_a]),              position of mu_b
   // with lambda_D = lambda_a + n_a lambda_b and mu_D = mu_b + n_b mu_a when the
   // last cycle is split (n_a > 1); otherwise lambda_b = lambda_D, mu_b = mu_D.
   std::vector<std::vector<i64>> genA(g.begin(), g.end() - 1), genC(h.begin(), h.end() - 1);
+  if (swap2) {
+    std::swap(genA[0], genA[1]);
+    std::swap(genC[0], genC[1]);
+  }
   std::vector<i64> gB = g[D - 1], hE = h[D - 1];
   if (na > 1) {
     genA.push_back(g[D - 1]);
@@ -515,6 +545,7 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
     i64 beta = cf % nD;
     for (int j = 0; j + 1 < D; ++j) alpha[j] = int(posmod(P.MU[j][d - 1], P.n[j]));
     if (na > 1) alpha[npen - 1] = int((cf / nD) % na);
+    if (swap2) std::swap(alpha[0], alpha[1]);
     const i64 gg = beta == 0 ? nD : gcd64(beta, nD);
     const i64 span = nD / gg;
     const i64 inv = span > 1 ? modinv(beta / gg, span) : 0;
@@ -694,11 +725,17 @@ pfft_status pfft::plan_device(pfft_plan_s& P) {
     const int Rm = P.dtype == PFFT_C64 ? 32 : 16;
     const int lr = Rm == 32 ? 5 : 4;
     base.push_back(idx.size());
+    // two pencil axes (fft_fast2.cuh): from span top on, the twiddle of k at
+    // span Ns is that of floor(k / top) at span Ns / top (the axes uncoupled)
+    const int top = (p == &P.colp && p->nsub == 2) ? p->sub_n[0] : 0;
     int Ns = p->fast_tail;
     for (int s = 0; s < p->fast_nmain; ++s) {
-      const int NsR = Ns * Rm;
-      for (int k = 0; k < Ns; ++k)
-        for (int b = 0; b < lr; ++b) idx.push_back(int(((int64_t(k) << b) % NsR) * (nD / NsR)));
+      const bool two = top && Ns >= top;
+      const int NsR = (two ? Ns / top : Ns) * Rm;
+      for (int k = 0; k < Ns; ++k) {
+        const int kk = two ? k / top : k;
+        for (int b = 0; b < lr; ++b) idx.push_back(int(((int64_t(kk) << b) % NsR) * (nD / NsR)));
+      }
       Ns *= Rm;
     }
     while (idx.size() - base.back() < size_t(p->stw_n)) idx.push_back(0);

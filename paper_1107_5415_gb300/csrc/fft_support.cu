@@ -96,6 +96,12 @@ __global__ void index_probe_kernel(PassArgs a, const int* __restrict__ PI, int w
   // split last cycle lambda_D = lambda_a + n_a lambda_b (input) and
   // mu_D = mu_b + n_b mu_a (output), lambda_a / mu_a the fastest row index.
   int64_t smith = w;
+  if (a.nsub == 2 && a.fs_na == 1 && a.sub_n[0] > a.sub_n[1]) {
+    // rows over (lambda_2, lambda_1): the planner put the longer axis first
+    // for the two-axis column pass (cycles are otherwise ascending)
+    const int l2 = row / a.sub_n[1], l1 = row - l2 * a.sub_n[1];
+    smith = (int64_t(l1) * a.sub_n[0] + l2) * a.nD + e;
+  }
   if (a.fs_na > 1) {
     const int ra = row % a.fs_na, rest = row / a.fs_na;
     const int64_t n = int64_t(a.fs_na) * a.nD;

@@ -41,6 +41,9 @@ SMALL = [
     [[11, 3, 5], [0, 13, 2], [0, 0, 4]],    # 572 = 4 * 11 * 13 in d = 3
     [[509, 0], [0, 67]],                    # cyclic 34103 = 509 * 67: split, direct stages in both passes
     [[23, 7], [0, 46]],                     # (23, 46): odd column tile count
+    [[32, 0, 16], [0, 16, 6], [0, 0, 4]],   # (2, 32, 32): register-resident column pass over two axes
+    [[32, 0, 16], [0, 8, 4], [0, 0, 16]],   # (4, 32, 32): the same, tail radix 4
+    [[64, 0, 48], [0, 16, 8], [0, 0, 16]],  # (8, 32, 64): the same, tail radix 8
 ]
 
 
@@ -168,6 +171,24 @@ def test_inverse_equals_conjugated_forward_of_the_transpose(M, batch):
     A.check_device_status()
     B.check_device_status()
     assert (torch.linalg.vector_norm(back - alt) / torch.linalg.vector_norm(back)).item() <= 1e-5
+
+
+@pytest.mark.parametrize("M", [[[32, 64, 0], [0, 64, 64], [0, 0, 64]], [[64, 0, 0], [0, 32, 0], [0, 0, 128]]])
+def test_two_axis_column_pass_with_swapped_axes_sampled(M):
+    """Cycles (32, 64, n): the register-resident column pass over the pencil of
+    32 x 64 runs with the longer axis first (its stages start with radix 2 x 32);
+    sampled frequencies, the round trip and the device index maps."""
+    plan = pf.PatternFFT(M, 2)
+    m = plan.m
+    c = SI.complex_normal(2, m, 17)
+    y = plan.forward(_gpu(c)).cpu().numpy()
+    slots = SI.sample_slots(m, 512, seed=5)
+    assert rel_l2(y[1:2, slots], oracle.pattern_fft(M, c[1:2], out_slots=slots)) <= 1e-5
+    assert rel_l2(plan.inverse(_gpu(y)).cpu().numpy(), c) <= 1e-5
+    lam = plan.index_map(pf.PFFT_MAP_INPUT_SNF)
+    n = [int(e) for e in plan.eps if e > 1]
+    dev_in = plan.device_index_map(pf.PFFT_MAP_INPUT_BOX).cpu().numpy()
+    assert (dev_in[np.ravel_multi_index(tuple(lam.T), n)] == np.arange(m)).all()
 
 
 def test_autograd_3d_sampled_frequencies():
