@@ -238,3 +238,38 @@ def test_plan_argument_errors():
     with pytest.raises(pf.PfftError) as e:
         pf.pwt_plan_create([[3, 0], [0, 4]], [[[2, 0], [0, 1]]], 0, 0.0, 1)
     assert e.value.status == 4  # not integral (checked before the device)
+
+
+def test_header_constants_match_binding():
+    """Every PFFT_* / PWT_* enumerator of include/pfft.h has the same value in
+    the ctypes binding (flags, dtypes, maps, symbols, batch flags)."""
+    src = open(os.path.join(ROOT, "include", "pfft.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, re.S):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            name, _, val = (x.strip() for x in item.partition("="))
+            nxt = int(val.rstrip("uU"), 0) if val else nxt
+            consts[name] = nxt
+            nxt += 1
+    checked = 0
+    for name, val in consts.items():
+        if hasattr(_capi, name):
+            assert getattr(_capi, name) == val, name
+            checked += 1
+    assert checked >= 15
+    for name in ("PFFT_FLAG_TC_SPLIT", "PFFT_FLAG_LAYOUT_SNF", "PFFT_FLAG_AUTOTUNE", "PFFT_FLAG_TRANSPOSED",
+                 "PFFT_BATCH_ONE_LAUNCH"):
+        assert name in consts and hasattr(_capi, name)
+
+
+def test_unknown_plan_flags_are_rejected_on_the_host():
+    with pytest.raises(pf.PfftError) as e:
+        pf.pfft_plan_create([[4, 0], [0, 4]], 1, flags=16)
+    assert e.value.status == 1  # PFFT_ERR_ARG before any device work
+    with pytest.raises(ValueError):
+        pf.PatternFFT([[4, 0], [0, 4]], 1, route="sideways")
